@@ -1,0 +1,251 @@
+"""Pins for the oracle's MPS algebra and time step.
+
+Pins: exact FDTD equality of the untruncated step (Table 1 / Eq. 2 vs Eq. 17),
+the closed-form cosine recurrence of a discrete eigenmode, the closed-form
+QT-T ranks of separable fields, conservation of the leapfrog energy, matrices
+constructed with known singular values (Eckart-Young), and brute-force
+dense evaluation of sums, samples and products."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qtt_oracle as O
+
+ORDERS = [O.SEQUENTIAL, O.INTERLEAVED]
+BCS = [O.PERIODIC, O.ZERO]
+INF = 1 << 30
+
+
+def test_trunc_rank_rule():
+    s = np.array([4.0, 2.0, 1e-3, 4e-6, 3.9e-6, 0.0])
+    assert O.trunc_rank(s, 1e-6, 100) == 4  # 4e-6 == eps*sigma_1 is kept
+    assert O.trunc_rank(s, 1e-6, 2) == 2
+    assert O.trunc_rank(s, 0.0, 100) == 6
+    assert O.trunc_rank(np.zeros(5), 1e-6, 10) == 1
+    assert O.trunc_rank(s, 0.9, 10) == 1
+    assert O.discarded_weight(s, 2) == pytest.approx(1e-6 + 16e-12 + 3.9e-6 ** 2)
+
+
+def _rand_mps(d, ranks, rng):
+    return [rng.standard_normal((ranks[k], 2, ranks[k + 1])) for k in range(d)]
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_tt_svd_round_trip_and_sample(order):
+    n = 4
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((16, 16))
+    cores = O.mps_from_dense(u, n, order, 0.0, INF)
+    rec = O.mps_to_dense(cores, n, order)
+    assert np.linalg.norm(rec - u) / np.linalg.norm(u) < 1e-14
+    ix = rng.integers(0, 16, 20)
+    iz = rng.integers(0, 16, 20)
+    np.testing.assert_allclose(O.mps_sample(cores, n, order, ix, iz), u[ix, iz], rtol=1e-12, atol=1e-13)
+    # left-orthonormal cores (Eq. 8 by sequential SVDs)
+    for c in cores[:-1]:
+        M = c.reshape(-1, c.shape[2])
+        np.testing.assert_allclose(M.T @ M, np.eye(M.shape[1]), atol=1e-13)
+
+
+def test_product_state_is_one_hot():
+    for order in ORDERS:
+        u = O.mps_to_dense(O.product_state(5, 2, 3, order), 3, order)
+        ref = np.zeros((8, 8))
+        ref[5, 2] = 1.0
+        np.testing.assert_array_equal(u, ref)
+
+
+def test_mps_sum_is_dense_sum():
+    rng = np.random.default_rng(2)
+    n, d = 3, 6
+    A = _rand_mps(d, [1, 2, 3, 4, 3, 2, 1], rng)
+    B = _rand_mps(d, [1, 2, 2, 2, 2, 2, 1], rng)
+    C = O.product_state(3, 6, n, O.INTERLEAVED)
+    S = O.mps_sum([(2.0, A), (-0.5, B), (3.0, C)])
+    full = lambda M: O.mps_full(M)
+    np.testing.assert_allclose(full(S), 2 * full(A) - 0.5 * full(B) + 3 * full(C), rtol=1e-13, atol=1e-13)
+    assert O.mps_ranks(S) == [1, 5, 6, 7, 6, 5, 1]
+
+
+def _orth(m, k, rng):
+    Q, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    return Q
+
+
+def test_two_site_zipup_is_best_rank_r_approximation():
+    """d = 2: the zip-up's single SVD sees the whole (2 x 2) ... here a
+    (2 x 2w)-site matrix built with prescribed singular values, so the
+    truncated result must be U_r S_r V_r^T exactly (Eckart-Young)."""
+    rng = np.random.default_rng(3)
+    # identity MPO on 2 sites with a bond-1 MPS of shape [1][2][4][..]: use
+    # a 2-site MPS whose matrix M = A1 A2 has rank 2 with s = (3, 1e-3)
+    U = _orth(2, 2, rng)
+    V = _orth(2, 2, rng)
+    s = np.array([3.0, 1e-3])
+    M = U @ np.diag(s) @ V.T
+    A = [M.reshape(1, 2, 2), np.eye(2).reshape(2, 2, 1)]
+    Id = [np.eye(2).reshape(1, 2, 2, 1)] * 2
+    out = O.zipup_lr(Id, A, 1e-2, 10)
+    got = O.mps_full(out).reshape(2, 2)
+    np.testing.assert_allclose(got, s[0] * np.outer(U[:, 0], V[:, 0]), atol=1e-14)
+    out = O.zipup_lr(Id, A, 1e-4, 10)
+    np.testing.assert_allclose(O.mps_full(out).reshape(2, 2), M, atol=1e-14)
+
+
+def test_round_truncates_to_prescribed_schmidt_values():
+    """3 sites, bond 2 carries Schmidt values (2, 0.1) by construction:
+    rounding with eps = 0.1 discards 0.1 < 0.1*2 and leaves the rank-1 term."""
+    rng = np.random.default_rng(4)
+    Lf = _orth(4, 2, rng)  # sites 1-2 -> bond 2, orthonormal columns
+    Rf = _orth(2, 2, rng)  # site 3
+    s = np.array([2.0, 0.1])
+    M = Lf @ np.diag(s) @ Rf.T  # (4 x 2): rows (s1, s2), columns s3
+    A = O.tt_svd(M.reshape(2, 2, 2), 0.0, INF)
+    B = O.tt_round(O.mps_sum([(0.5, A), (0.5, A)]), 0.1, 10)
+    assert O.mps_ranks(B)[2] == 1
+    np.testing.assert_allclose(O.mps_full(B).reshape(4, 2), s[0] * np.outer(Lf[:, 0], Rf[:, 0]), atol=1e-12)
+    B = O.tt_round(O.mps_sum([(0.5, A), (0.5, A)]), 0.04, 10)
+    assert O.mps_ranks(B)[2] == 2
+    np.testing.assert_allclose(O.mps_full(B).reshape(4, 2), M, atol=1e-12)
+
+
+def test_round_of_doubled_state_recovers_state_and_ranks():
+    rng = np.random.default_rng(5)
+    d = 8
+    ranks = [1, 2, 4, 5, 6, 5, 4, 2, 1]
+    A = _rand_mps(d, ranks, rng)
+    B = O.tt_round(O.mps_sum([(1.0, A), (1.0, A)]), 1e-12, INF)
+    assert O.mps_ranks(B) == ranks
+    np.testing.assert_allclose(O.mps_full(B), 2 * O.mps_full(A), rtol=1e-11, atol=1e-11)
+    # right-orthonormal cores 2..d after the right-to-left SVD sweep
+    for c in B[1:]:
+        M = c.reshape(c.shape[0], -1)
+        np.testing.assert_allclose(M @ M.T, np.eye(M.shape[0]), atol=1e-12)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_zipups_untruncated_equal_dense_operators(order, bc):
+    n = 3
+    rng = np.random.default_rng(6)
+    u = rng.standard_normal((8, 8))
+    c2 = rng.uniform(1.0, 4.0, (8, 8))
+    A = O.mps_from_dense(u, n, order, 0.0, INF)
+    L = O.laplacian_mpo(n, order, bc)
+    phi = O.zipup_lr(L, A, 0.0, INF)
+    Lu = (O.neighbour_sum(u, bc) - 4.0 * u)
+    np.testing.assert_allclose(O.mps_to_dense(phi, n, order), Lu, rtol=1e-12, atol=1e-12)
+    C = O.mps_from_dense(c2, n, order, 0.0, INF)
+    eta = O.zipup_rl(O.diagonal_mpo(C), phi, 0.0, INF)
+    np.testing.assert_allclose(O.mps_to_dense(eta, n, order), c2 * Lu, rtol=1e-12, atol=1e-11)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_untruncated_mps_step_equals_fdtd(order, bc):
+    """Table 1: Eq. 17 in MPS form is the Eq. 2 update (chi = inf, eps = 0)."""
+    n = 3
+    rng = np.random.default_rng(7)
+    c = rng.uniform(1500.0, 3000.0, (8, 8))
+    c2 = c * c
+    lam2 = (0.5 / c.max()) ** 2
+    C = O.velocity_mps(c, n, order, 0.0, INF)
+    c2r = O.mps_to_dense(C, n, order)
+    np.testing.assert_allclose(c2r, c2, rtol=1e-13)
+    L = O.laplacian_mpo(n, order, bc)
+    d = 2 * n
+    prev, cur = O.zero_mps(d), O.zero_mps(d)
+    up, uc = np.zeros((8, 8)), np.zeros((8, 8))
+    src = (3, 5)
+    for k in range(25):
+        amp = math.sin(0.3 * k) + 0.1 * k
+        nxt = O.mps_step(L, C, lam2, prev, cur, 0.0, INF, src, amp, n, order)
+        un = O.fdtd_step(up, uc, c2r, lam2, bc, src, amp)
+        prev, cur = cur, nxt
+        up, uc = uc, un
+    got = O.mps_to_dense(cur, n, order)
+    assert np.linalg.norm(got - uc) / np.linalg.norm(uc) < 1e-12
+
+
+def _mode(n, p, q, bc):
+    N = 1 << n
+    x = np.arange(N)
+    if bc == O.PERIODIC:
+        fx = np.cos(2 * np.pi * p * x / N)
+        fz = np.cos(2 * np.pi * q * x / N)
+        mu = -4 * math.sin(math.pi * p / N) ** 2 - 4 * math.sin(math.pi * q / N) ** 2
+    else:
+        fx = np.sin(np.pi * p * (x + 1) / (N + 1))
+        fz = np.sin(np.pi * q * (x + 1) / (N + 1))
+        mu = (2 * math.cos(math.pi * p / (N + 1)) - 2) + (2 * math.cos(math.pi * q / (N + 1)) - 2)
+    return np.outer(fx, fz), mu
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("order", ORDERS)
+def test_eigenmode_follows_cosine_recurrence(bc, order):
+    """Constant c, u^0 = mode, u^{-1} = cos(theta) u^0 with
+    cos(theta) = 1 + lambda^2 c^2 mu / 2: then u^k = cos(k theta) u^0 exactly."""
+    n = 5
+    u0, mu = _mode(n, 1, 2, bc)
+    lam2c2 = 0.25
+    ct = 1.0 + lam2c2 * mu / 2.0
+    th = math.acos(ct)
+    C = O.velocity_mps(np.ones((32, 32)), n, order, 1e-14, 8)  # c = 1, so lambda^2 = 0.25
+    L = O.laplacian_mpo(n, order, bc)
+    cur = O.mps_from_dense(u0, n, order, 1e-14, 8)
+    prev = O.mps_from_dense(ct * u0, n, order, 1e-14, 8)
+    for k in range(1, 121):
+        prev, cur = cur, O.mps_step(L, C, lam2c2, prev, cur, 1e-13, 16)
+        assert max(O.mps_ranks(cur)) <= 4
+    got = O.mps_to_dense(cur, n, order)
+    np.testing.assert_allclose(got, math.cos(120 * th) * u0, atol=1e-10)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_separable_fields_have_closed_form_ranks(order):
+    n = 5
+    N = 1 << n
+    x = np.arange(N, dtype=float)
+    fams = {
+        "exp": (np.exp(0.07 * x), lambda m: 1),
+        "cos": (np.cos(0.3 * x + 0.2), lambda m: 1 if m in (0, n) else 2),
+        "poly2": (1 + 0.5 * (x / N) - 2 * (x / N) ** 2, lambda m: min(3, 2 ** m, 2 ** (n - m))),
+        "delta": ((x == 9).astype(float), lambda m: 1),
+    }
+    for fa, (f, rf) in fams.items():
+        for ga, (g, rg) in fams.items():
+            cores = O.mps_from_dense(np.outer(f, g), n, order, 1e-12, INF)
+            ranks = O.mps_ranks(cores)
+            # rf(m): rank of f unfolded as (bits < m) x (bits >= m)
+            if order == O.SEQUENTIAL:
+                exp = [1] + [rf(k) for k in range(1, n)] + [1] + [rg(k) for k in range(1, n)] + [1]
+            else:
+                exp = [1]
+                for lev in range(n):  # sites x_lev, z_lev
+                    exp.append(rf(lev + 1) * rg(lev))  # after x_lev: x bits <= lev, z bits < lev
+                    exp.append(rf(lev + 1) * rg(lev + 1))
+                exp[-1] = 1
+            assert ranks == exp, (fa, ga, ranks, exp)
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_leapfrog_energy_is_conserved_by_untruncated_mps_step(bc):
+    n = 3
+    order = O.INTERLEAVED
+    rng = np.random.default_rng(8)
+    c = rng.uniform(1.0, 2.0, (8, 8))
+    c2 = c * c
+    lam2 = 0.45 / c2.max()  # lam^2 c^2 <= 0.45 < 1/2 (stable)
+    C = O.velocity_mps(c, n, order, 0.0, INF)
+    L = O.laplacian_mpo(n, order, bc)
+    u_prev, u_cur = rng.standard_normal((8, 8)), rng.standard_normal((8, 8))
+    prev = O.mps_from_dense(u_prev, n, order, 0.0, INF)
+    cur = O.mps_from_dense(u_cur, n, order, 0.0, INF)
+    c2r = O.mps_to_dense(C, n, order)
+    E0 = O.leapfrog_energy(u_prev, u_cur, c2r, lam2, bc)
+    for _ in range(40):
+        prev, cur = cur, O.mps_step(L, C, lam2, prev, cur, 0.0, INF)
+    E = O.leapfrog_energy(O.mps_to_dense(prev, n, order), O.mps_to_dense(cur, n, order), c2r, lam2, bc)
+    assert abs(E - E0) < 1e-11 * abs(E0)
