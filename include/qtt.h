@@ -1,0 +1,222 @@
+/*
+ * qtt.h -- C ABI of the B300 (sm_103a) MPS / quantized-tensor-train stepper
+ * for the explicit 2D acoustic FDTD scheme.
+ *
+ * Paper: "Quantum Circuit and Tensor Network Implementation of the 2D Acoustic
+ * Wave Equation" (Nemeth & Vattay).  One time step (Eq. 17, Table 1) is
+ *
+ *     phi       = L psi^k                  (Laplacian MPO, Eq. 16, by zip-up)
+ *     eta       = C^2 phi                  (diagonal MPO of c^2, Eq. 4, Sec. 4.3)
+ *     theta     = 2 psi^k - psi^{k-1} + lambda^2 eta [+ s_k e_src]
+ *     psi^{k+1} = round(theta)             (QR sweep, then truncated-SVD sweep,
+ *                                           Sec. 4.3)
+ *
+ * Conventions shared by every call:
+ *   - Grid: N = 2^n points per axis; dense fields are double, row-major
+ *     u[x * N + z] with x horizontal and z depth (Sec. 2, Eq. 2).
+ *   - Sites: d = 2n binary sites in the tensor-product order of Eq. 12, the
+ *     least significant bit first.  QTT_ORDER_SEQUENTIAL: x_0..x_{n-1} then
+ *     z_0..z_{n-1} (Eq. 14-15); QTT_ORDER_INTERLEAVED: x_0, z_0, x_1, z_1, ...
+ *   - MPS core k (k = 0..d-1) is a double array [r_k][2][r_{k+1}], row-major,
+ *     r_0 = r_d = 1 (Eq. 8).  MPO core k is [w_k][2 out][2 in][w_{k+1}].
+ *   - Truncation (Sec. 4.3): keep sigma_i >= eps * sigma_1, at most chi_max
+ *     values, at least one.
+ *   - Every function returns a qtt_status; nothing throws across the ABI.
+ *     QTT_EINVAL is returned before any launch for bad arguments; the text of
+ *     the last error of the calling thread is given by qtt_last_error().
+ *   - Work is queued asynchronously on the context's CUDA stream.  Failures
+ *     detected on the device (a Jacobi sweep limit, a grid-barrier timeout, a
+ *     non-finite value) are recorded in a device status word and returned by
+ *     the next call that synchronises (qtt_ctx_sync, qtt_mps_ranks,
+ *     qtt_mps_get_cores).
+ *   - Ownership: handles and their device buffers belong to the library and
+ *     are released by the matching *_destroy.  Caller buffers marked "device"
+ *     are device pointers on the context's device (e.g. torch tensors); they
+ *     are read or written on the context stream.
+ *   - There is no CPU fallback: every call needs a CUDA device.
+ */
+#ifndef QTT_H
+#define QTT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QTT_OK = 0,
+  QTT_EINVAL = 1,      /* bad argument, nothing launched */
+  QTT_ENOMEM = 2,      /* device allocation failed */
+  QTT_ECUDA = 3,       /* a CUDA runtime call failed */
+  QTT_ENOCONV = 4,     /* Jacobi SVD hit its sweep limit */
+  QTT_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  QTT_ENONFINITE = 6   /* NaN/Inf met in a singular-value spectrum */
+} qtt_status;
+
+typedef enum { QTT_ORDER_SEQUENTIAL = 0, QTT_ORDER_INTERLEAVED = 1 } qtt_order;
+typedef enum { QTT_BC_PERIODIC = 0, QTT_BC_ZERO = 1 } qtt_bc;
+typedef enum { QTT_FP64 = 0, QTT_TF32 = 1, QTT_BF16 = 2, QTT_FP32 = 3 } qtt_precision;
+
+/* Solver parameters.  n: bits per axis (1..14).  order: qtt_order.  bc:
+ * qtt_bc; PERIODIC is the cyclic shift |x> -> |(x+1) mod 2^n> of Sec. 3.1 and
+ * Sec. 4.2, ZERO is the terminal tensor of Eq. 11 as printed (the overflow is
+ * dropped, i.e. u = 0 outside the grid).  prec: arithmetic of the
+ * contractions (qtt_precision; QTT_FP64 is the plain form).  chi_max, eps:
+ * truncation of the state (Sec. 4.3).  chi_zip, eps_zip: truncation inside
+ * the two zip-up applications (0 = use chi_max / eps).  chi_c, eps_c:
+ * truncation of the c^2 MPS (the paper does not say; 0 = chi_max / 1e-8).
+ * use_learned_rank: reserved, must be 0. */
+typedef struct {
+  int n;
+  int order;
+  int bc;
+  int prec;
+  int chi_max;
+  double eps;
+  int chi_zip;
+  double eps_zip;
+  int chi_c;
+  double eps_c;
+  int use_learned_rank;
+} qtt_params;
+
+typedef struct qtt_ctx qtt_ctx;
+typedef struct qtt_mps qtt_mps;
+typedef struct qtt_mpo qtt_mpo;
+
+/* Create a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream); the caller keeps it alive
+ * until qtt_ctx_destroy.  The context owns its workspace. */
+qtt_status qtt_ctx_create(const qtt_params* params, void* cuda_stream, qtt_ctx** out);
+void qtt_ctx_destroy(qtt_ctx* ctx);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* qtt_last_error(void);
+
+/* Wait for the context stream and return (then clear) the device status. */
+qtt_status qtt_ctx_sync(qtt_ctx* ctx);
+
+/* ------------------------------------------------------------------ states */
+
+/* Rank-1 MPS of the zero field (the zero initial condition). */
+qtt_status qtt_mps_create_zero(qtt_ctx* ctx, qtt_mps** out);
+
+/* MPS of a dense field: sequential truncated SVDs (TT-SVD, Eq. 8) with
+ * (chi_max, eps), then the compression of Sec. 4.3 (QR sweep, SVD sweep),
+ * so that cores 1..d-1 are right-orthonormal as qtt_step expects.  grid: N*N
+ * doubles u[x*N+z], device memory if on_device else host memory (copied;
+ * the call waits for it).  Synchronises. */
+qtt_status qtt_mps_from_dense(qtt_ctx* ctx, const double* grid, int on_device, qtt_mps** out);
+
+/* MPS from explicit cores.  ranks: d+1 host ints (ranks[0] = ranks[d] = 1,
+ * each rank >= 1 and <= the context's capacity min(2^k, 2^(d-k), chi_max));
+ * cores: host doubles, core 0..d-1 concatenated, each [r_k][2][r_{k+1}]. */
+qtt_status qtt_mps_from_cores(qtt_ctx* ctx, const int* ranks, const double* cores, qtt_mps** out);
+
+/* Copy an MPS to the host: ranks (d+1 ints) and, if cores is not NULL, the
+ * concatenated cores (capacity given in doubles by cores_capacity; the
+ * needed size is sum_k r_k*2*r_{k+1}).  Synchronises the stream. */
+qtt_status qtt_mps_get_cores(qtt_ctx* ctx, const qtt_mps* psi, int* ranks, double* cores,
+                             long cores_capacity);
+
+/* Current bond dimensions r_0..r_d (d+1 host ints).  Synchronises. */
+qtt_status qtt_mps_ranks(qtt_ctx* ctx, const qtt_mps* psi, int* ranks_out);
+void qtt_mps_destroy(qtt_mps* psi);
+
+/* MPS of the squared velocity c^2(x,z) (the diagonal operator C^2 of Eq. 4,
+ * used as a diagonal MPO in Sec. 4.3), by TT-SVD (Eq. 8) with
+ * (chi_c, eps_c).  c_grid: N*N velocities (m/s, > 0), device if on_device
+ * else host.  Synchronises (the c^2 ranks are fixed for the run). */
+qtt_status qtt_velocity_mps(qtt_ctx* ctx, const double* c_grid, int on_device, qtt_mps** c2_out);
+
+/* Laplacian MPO S_x^+ + S_x^- + S_z^+ + S_z^- - 4I (Eq. 16) built from the
+ * carry tensors of Eq. 9-13 as one five-state carry automaton, for the
+ * context's order and boundary condition.  Built on the host, copied once. */
+qtt_status qtt_laplacian_mpo(qtt_ctx* ctx, qtt_mpo** out);
+/* Bond dimensions w_0..w_d of an MPO (d+1 host ints). */
+qtt_status qtt_mpo_bonds(const qtt_mpo* L, int* bonds_out);
+void qtt_mpo_destroy(qtt_mpo* L);
+
+/* ------------------------------------------------------------------- step */
+
+/* psi <- round(psi + amp * e_(ix,iz)): a rank-1 product-state add (the
+ * impulsive source of Sec. 5) followed by the Sec. 4.3 compression. */
+qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, double amp);
+
+/* One time step of Eq. 17.  On entry psi_prev = u^{k-1}, psi_cur = u^k; on
+ * return psi_prev = u^k and psi_cur = u^{k+1} (the handles exchange their
+ * buffers; nothing is reallocated).  lambda2 = (dt/dh)^2 (Eq. 2).
+ * src_ixiz: NULL for no source, else a host pair {ix, iz} where src_amp is
+ * added to u^{k+1} as a rank-1 product state.  psi_cur must be right-
+ * orthonormal in cores 1..d-1 (as every state this library returns is) for
+ * the zip-up truncation to measure the right norm. */
+qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2,
+                    qtt_mps* psi_prev, qtt_mps* psi_cur, const long* src_ixiz, double src_amp);
+
+/* ---------------------------------------------------------------- readout */
+
+/* Receiver readout: out[p] = A_0[s_0] A_1[s_1] ... A_{d-1}[s_{d-1}] (Eq. 8)
+ * at grid points (ix[p], iz[p]), p < count.  ix, iz, out: device arrays of
+ * count int64 / int64 / double.  Indices are not range-checked on the
+ * device; the caller keeps them in [0, N). */
+qtt_status qtt_sample(qtt_ctx* ctx, const qtt_mps* psi, const long* ix_dev, const long* iz_dev,
+                      long count, double* out_dev);
+
+/* Full contraction to the dense grid: out_dev[x*N+z], N*N device doubles. */
+qtt_status qtt_to_dense(qtt_ctx* ctx, const qtt_mps* psi, double* out_dev);
+
+/* ------------------------------------------------------- linear algebra */
+
+/* Truncated SVD of one bond matrix with the Sec. 4.3 rule, the factorisation
+ * every truncation in the step uses: M = U S V^T, M an (m x n) row-major
+ * device matrix (not modified).  Writes r = kept rank to *rank_out (host)
+ * and, on the device, U (m x r, row-major, ld r), S (r values, descending)
+ * and Vt (r x n, row-major, ld n); out buffers hold at least m*min(m,n),
+ * min(m,n) and min(m,n)*n doubles.  chi <= 0 means no cap.  Synchronises. */
+qtt_status qtt_svd_trunc(qtt_ctx* ctx, const double* M_dev, int m, int n, double eps, int chi,
+                         double* U_dev, double* S_dev, double* Vt_dev, int* rank_out);
+
+/* ------------------------------------------------------------- context */
+
+/* Dense FDTD update of Eq. 2 on the device (the scheme the MPS step
+ * reproduces; used for comparison runs):
+ * u_next = 2 u_cur - u_prev + lambda2 * c2 * (4-neighbour sum - 4 u_cur),
+ * plus amp at (src_ix, src_iz) when src_ix >= 0.  All arrays N*N device
+ * doubles; boundary rule from the context. */
+qtt_status qtt_fdtd_step(qtt_ctx* ctx, const double* c2_dev, double lambda2, const double* u_prev_dev,
+                         const double* u_cur_dev, double* u_next_dev, long src_ix, long src_iz,
+                         double amp);
+
+/* Singular values, kept ranks and discarded weights of the last step, for
+ * diagnostics.  discarded: 3*(d-1) host doubles (zip-up L bonds 1..d-1,
+ * zip-up C^2 bonds 1..d-1, rounding bonds 1..d-1).  Synchronises. */
+qtt_status qtt_last_step_discarded(qtt_ctx* ctx, double* discarded);
+
+/* --------------------------------------------------------- measurement */
+
+/* Kernel classes counted by qtt_profile: 0 GEMM contraction, 1 Householder
+ * QR, 2 Jacobi SVD, 3 sort/truncate (Sec. 4.3 rule), 4 MPO application,
+ * 5 MPS sum, 6 copy/transpose, 7 dense FDTD, 8 other. */
+#define QTT_KCLASSES 9
+
+typedef struct {
+  long launches[QTT_KCLASSES]; /* kernels launched since qtt_profile_start */
+  double ms[QTT_KCLASSES];     /* device time of those launches (timing on) */
+  long svd_logged;             /* Jacobi launches whose size was logged */
+  double svd_flops;            /* sum of 6 m n^2 + 20 n^3 over them (n <= m:
+                                  the two sizes of the rotated problem) */
+} qtt_profile;
+
+/* Reset the counters of the context.  timing != 0 brackets every launch with
+ * CUDA events on the context stream (adds a little host work per launch);
+ * log_svd != 0 records the size of up to 65536 Jacobi launches.  Counting
+ * launches is always on. */
+qtt_status qtt_profile_start(qtt_ctx* ctx, int timing, int log_svd);
+
+/* Read the counters (synchronises the stream). */
+qtt_status qtt_profile_read(qtt_ctx* ctx, qtt_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTT_H */

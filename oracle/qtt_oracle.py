@@ -139,6 +139,13 @@ def mps_from_dense(u: np.ndarray, n: int, order: str, eps: float, chi: int) -> l
     return tt_svd(dense_to_tensor(u, n, order), eps, chi)
 
 
+def state_from_dense(u: np.ndarray, n: int, order: str, eps: float, chi: int) -> list[np.ndarray]:
+    """A state for the stepper: TT-SVD (Eq. 8), then the Sec. 4.3 compression,
+    which leaves cores 2..d right-orthonormal (the zip-up of Eq. 16 sweeps
+    from site 1 and measures the truncation in that gauge)."""
+    return tt_round(mps_from_dense(u, n, order, eps, chi), eps, chi)
+
+
 def velocity_mps(c: np.ndarray, n: int, order: str, eps_c: float, chi_c: int) -> list[np.ndarray]:
     """MPS of the squared velocity c^2(x, z) (Eq. 4), by TT-SVD (Eq. 8)."""
     c = np.asarray(c, dtype=np.float64)
@@ -374,7 +381,7 @@ def zipup_lr(W: list[np.ndarray], A: list[np.ndarray], eps: float, chi: int,
     C = np.ones((1, 1, 1))
     out = []
     for k in range(d):
-        T = np.einsum("awb,bsc,wtsv->atvc", C, A[k], W[k])
+        T = np.einsum("awb,bsc,wtsv->atvc", C, A[k], W[k], optimize=True)
         a, _t, wv, bc = T.shape
         M = T.reshape(a * 2, wv * bc)
         if k == d - 1:
@@ -399,7 +406,7 @@ def zipup_rl(W: list[np.ndarray], A: list[np.ndarray], eps: float, chi: int,
     C = np.ones((1, 1, 1))
     out: list = [None] * d
     for k in range(d - 1, -1, -1):
-        T = np.einsum("bsc,wtsv,cva->bwta", A[k], W[k], C)
+        T = np.einsum("bsc,wtsv,cva->bwta", A[k], W[k], C, optimize=True)
         b, w, _t, a = T.shape
         M = T.reshape(b * w, 2 * a)
         if k == 0:

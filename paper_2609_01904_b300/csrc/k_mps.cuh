@@ -1,0 +1,61 @@
+// Launchers of the MPS-level kernels (k_mps.cu).
+#pragma once
+
+#include "qtt_internal.cuh"
+
+namespace qtt {
+
+constexpr int kMaxSites = 32;
+constexpr int kMaxTerms = 4;
+
+struct SumArgs {
+  int d;
+  int nterms;  // MPS terms (the rank-1 source is extra)
+  const double* core[kMaxTerms][kMaxSites];
+  const int* ranks[kMaxTerms];
+  double coef[kMaxTerms];
+  double* out[kMaxSites];
+  int* out_ranks;
+  int has_src;
+  int src_bits[kMaxSites];
+  double src_amp;
+};
+
+struct SampleArgs {
+  int d, n, order, rmax;
+  const double* core[kMaxSites];
+  const int* ranks;
+  const long* ix;
+  const long* iz;
+  long long count;
+  double* out;
+};
+
+struct ChainArgs {
+  int d, h, rmax;
+  const double* core[kMaxSites];
+  const int* ranks;
+  double* out;
+};
+
+cudaError_t mpo_apply_lr(const double* X, double* T, const double* W, int w, int w2, const int* a_p, const int* b2_p,
+                         long long total_max, cudaStream_t st);
+cudaError_t mps_sum(const SumArgs& a, long long max_core_elems, cudaStream_t st);
+cudaError_t sample(const SampleArgs& a, cudaStream_t st);
+cudaError_t chains(const ChainArgs& left, const ChainArgs& right, cudaStream_t st);
+cudaError_t scatter_dense(const double* S, double* out, int n, int order, int h, cudaStream_t st);
+cudaError_t site_permute(const double* u, double* t, int n, int order, bool square, cudaStream_t st);
+cudaError_t fdtd(const double* c2, double lambda2, const double* up, const double* uc, double* un, int n, int bc,
+                 long long sx, long long sz, double amp, cudaStream_t st);
+cudaError_t copy2d(const double* src, double* dst, Dim R, Dim C, Dim ssi, Dim ssj, Dim dsi, Dim dsj,
+                   long long total_max, double alpha, cudaStream_t st);
+cudaError_t init_zip(double* carry, int* ranks, int d, const int* copy_src, int* copy_dst, int ncopy,
+                     cudaStream_t st);
+cudaError_t scale_rows(double* M, long long ldm, Dim ncols, const int* r_p, const double* sigma, long long total_max,
+                       cudaStream_t st);
+
+// k_linalg.cu
+cudaError_t linalg_init(int device);
+int coop_max_blocks(int num_sms);
+
+}  // namespace qtt

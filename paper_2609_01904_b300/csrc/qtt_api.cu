@@ -1,0 +1,1133 @@
+// C ABI of the QTT stepper: handles, workspace and the orchestration of one
+// time step (Eq. 17) as a sequence of launches on the context stream with
+// every bond rank kept in device memory (no host synchronisation per step).
+#include <algorithm>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "k_mps.cuh"
+#include "qtt_internal.cuh"
+
+namespace qtt {
+void build_laplacian(int n, int order, int bc, Mpo* mpo);
+}
+
+using namespace qtt;
+
+namespace {
+
+thread_local std::string g_err;
+
+qtt_status fail(qtt_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? QTT_ENOMEM : QTT_ECUDA,                    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+// Every kernel launch goes through KL: it counts the launch and, when kernel
+// timing is on, brackets it with events on the context stream.
+#define KL_N(cls, nk, call)                                                                    \
+  do {                                                                                         \
+    prof_begin(ctx, cls);                                                                      \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? QTT_ENOMEM : QTT_ECUDA,                    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+    prof_end(ctx, cls, nk);                                                                    \
+  } while (0)
+#define KL(cls, call) KL_N(cls, 1, call)
+#define KL2(cls, call) KL_N(cls, 2, call)
+
+void prof_begin(qtt_ctx* ctx, int cls) {
+  Prof& p = ctx->prof;
+  if (!p.timing) return;
+  if (p.used >= (int)p.ev.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      p.timing = 0;
+      return;
+    }
+    p.ev.push_back({a, b});
+  }
+  cudaEventRecord(p.ev[p.used].first, ctx->stream);
+  p.cls.resize(p.ev.size());
+  p.cls[p.used] = cls;
+}
+
+void prof_end(qtt_ctx* ctx, int cls, int nk) {
+  Prof& p = ctx->prof;
+  p.launches[cls] += nk;
+  if (!p.timing) return;
+  cudaEventRecord(p.ev[p.used].second, ctx->stream);
+  ++p.used;
+}
+
+#define CKS(expr)                  \
+  do {                             \
+    qtt_status s_ = (expr);        \
+    if (s_ != QTT_OK) return s_;   \
+  } while (0)
+
+inline long long p2(int e) { return e >= 62 ? (1LL << 62) : (1LL << e); }
+
+// -------------------------------------------------------------- MPS memory
+std::vector<int> psi_caps(int d, int chi) {
+  std::vector<int> c(d + 1);
+  for (int k = 0; k <= d; ++k) c[k] = (int)std::min<long long>({p2(k), p2(d - k), (long long)chi});
+  return c;
+}
+
+qtt_status mps_alloc(qtt_ctx* ctx, const std::vector<int>& cap, Mps* m) {
+  m->ctx = ctx;
+  m->d = ctx->d;
+  m->cap = cap;
+  m->off.assign(m->d, 0);
+  long long tot = 0;
+  for (int k = 0; k < m->d; ++k) {
+    m->off[k] = tot;
+    tot += (long long)cap[k] * 2 * cap[k + 1];
+  }
+  m->total = tot;
+  CK(cudaMalloc(&m->data, std::max<long long>(tot, 1) * sizeof(double)));
+  CK(cudaMalloc(&m->ranks, (m->d + 1) * sizeof(int)));
+  CK(cudaMemsetAsync(m->data, 0, std::max<long long>(tot, 1) * sizeof(double), ctx->stream));
+  std::vector<int> ones(m->d + 1, 1);
+  CK(cudaMemcpyAsync(m->ranks, ones.data(), (m->d + 1) * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return QTT_OK;
+}
+
+void mps_free(Mps* m) {
+  if (!m) return;
+  if (m->data) cudaFree(m->data);
+  if (m->ranks) cudaFree(m->ranks);
+  m->data = nullptr;
+  m->ranks = nullptr;
+}
+
+// --------------------------------------------------------------- workspace
+struct Caps {
+  std::vector<int> psi, phi, eta, theta;
+};
+
+Caps step_caps(const qtt_ctx* ctx, const std::vector<int>& w, const std::vector<int>& rc) {
+  const int d = ctx->d, chi = ctx->p.chi_max, chz = ctx->p.chi_zip;
+  Caps c;
+  c.psi = psi_caps(d, chi);
+  c.phi.assign(d + 1, 1);
+  c.eta.assign(d + 1, 1);
+  c.theta.assign(d + 1, 1);
+  for (int k = 1; k < d; ++k)
+    c.phi[k] = (int)std::min<long long>({(long long)chz, p2(k), (long long)w[k] * c.psi[k]});
+  for (int k = 1; k < d; ++k)
+    c.eta[k] = (int)std::min<long long>({(long long)chz, p2(d - k), (long long)c.phi[k] * rc[k]});
+  for (int k = 1; k < d; ++k) c.theta[k] = 2 * c.psi[k] + c.eta[k] + 1;
+  return c;
+}
+
+void ws_free(qtt_ctx* ctx) {
+  Workspace& s = ctx->ws;
+  double** bufs[] = {&s.d_carry, &s.d_x, &s.d_tv, &s.d_tq, &s.d_rv, &s.d_jv, &s.d_jp, &s.d_w1,
+                     &s.d_tt, &s.d_qt, &s.d_jh, &s.d_tau, &s.d_sig, &s.d_norm, &s.d_disc};
+  for (double** b : bufs)
+    if (*b) {
+      cudaFree(*b);
+      *b = nullptr;
+    }
+  if (s.d_ints) cudaFree(s.d_ints);
+  s.d_ints = nullptr;
+  if (s.d_sync) cudaFree(s.d_sync);
+  s.d_sync = nullptr;
+  Mps* ms[] = {s.phi, s.eta, s.theta, s.spare};
+  for (Mps* m : ms)
+    if (m) {
+      mps_free(m);
+      delete m;
+    }
+  s.phi = s.eta = s.theta = s.spare = nullptr;
+  ctx->ws_ready = false;
+}
+
+struct Sizes {
+  long long carry = 1, x = 1, tv = 1, rv = 1, jv = 1, jp = 1, w1 = 1, vec = 1;
+  long long nvmax = 2, ellmax = 1;
+};
+
+// Largest buffer each phase needs, from the per-bond capacities.
+Sizes step_sizes(const qtt_ctx* ctx, const Caps& c, const std::vector<int>& w, const std::vector<int>& rc) {
+  const int d = ctx->d;
+  Sizes z;
+  auto upd = [](long long& a, long long b) { a = std::max(a, b); };
+  // zip-up L: site k, a = phi[k], w = w[k], b = psi[k], b' = psi[k+1], w' = w[k+1]
+  for (int k = 0; k < d; ++k) {
+    long long a = c.phi[k], b2 = c.psi[k + 1], wl = w[k], wr = w[k + 1];
+    upd(z.x, a * wl * 2 * b2);
+    upd(z.tv, 2 * a * wr * b2);
+    upd(z.carry, (long long)c.phi[k + 1] * wr * b2);
+    upd(z.nvmax, 2 * a);
+    upd(z.ellmax, wr * b2);
+  }
+  // zip-up C^2: site k, B = phi[k], B' = phi[k+1], R = rc[k], R' = rc[k+1], A' = eta[k+1]
+  for (int k = d - 1; k >= 0; --k) {
+    long long B = c.phi[k], B2 = c.phi[k + 1], R = rc[k], R2 = rc[k + 1], A2 = c.eta[k + 1];
+    upd(z.x, 2 * B * R2 * A2);
+    upd(z.tv, 2 * A2 * B * R);
+    upd(z.carry, B2 * R2 * A2);
+    upd(z.carry, B * R * (long long)c.eta[k]);
+    upd(z.nvmax, 2 * A2);
+    upd(z.ellmax, B * R);
+  }
+  // round: QR of (2 q_k) x D_{k+1}; SVD of q_k x 2 r_{k+1}
+  for (int k = 0; k < d; ++k) {
+    long long q = c.theta[k], D2 = c.theta[k + 1];
+    upd(z.tv, 2 * q * D2);
+    upd(z.rv, std::min(2 * q, D2) * D2);
+    upd(z.w1, (long long)c.psi[k] * q);
+    upd(z.nvmax, 2 * (long long)c.psi[k + 1]);
+    upd(z.ellmax, std::max(2 * q, q));
+    upd(z.vec, D2);
+    upd(z.vec, 2 * q);
+  }
+  // TT-SVD of a dense grid (c^2 with chi_c, states with chi_max)
+  upd(z.nvmax, 2LL * std::max(ctx->p.chi_max, ctx->p.chi_c));
+  upd(z.vec, z.nvmax);
+  upd(z.jv, z.nvmax * z.nvmax);
+  upd(z.jp, z.nvmax * z.nvmax);
+  upd(z.rv, z.nvmax * z.nvmax);
+  return z;
+}
+
+qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
+  Workspace& s = ctx->ws;
+  const int d = ctx->d;
+  const long long N2 = p2(2 * ctx->p.n);
+  // TT-SVD of a dense grid and to_dense use N^2-sized scratch
+  long long tv = std::max(z.tv, N2), carry = std::max(z.carry, N2), x = std::max(z.x, N2);
+  s.carry = carry;
+  s.xbuf = x;
+  s.tv = tv;
+  s.tq = tv;
+  s.rv = z.rv;
+  s.jv = z.jv;
+  s.jp = z.jp;
+  s.w1 = std::max(z.w1, 1LL);
+  s.vec = std::max(z.vec, 64LL);
+  CK(cudaMalloc(&s.d_carry, carry * sizeof(double)));
+  CK(cudaMalloc(&s.d_x, x * sizeof(double)));
+  CK(cudaMalloc(&s.d_tv, tv * sizeof(double)));
+  CK(cudaMalloc(&s.d_tq, tv * sizeof(double)));
+  CK(cudaMalloc(&s.d_rv, s.rv * sizeof(double)));
+  CK(cudaMalloc(&s.d_jv, s.jv * sizeof(double)));
+  CK(cudaMalloc(&s.d_jp, s.jp * sizeof(double)));
+  CK(cudaMalloc(&s.d_w1, s.w1 * sizeof(double)));
+  CK(cudaMalloc(&s.d_tt, tv * sizeof(double)));
+  CK(cudaMalloc(&s.d_qt, tv * sizeof(double)));
+  CK(cudaMalloc(&s.d_jh, s.jv * sizeof(double)));
+  CK(cudaMalloc(&s.d_tau, s.vec * sizeof(double)));
+  CK(cudaMalloc(&s.d_sig, s.vec * sizeof(double)));
+  CK(cudaMalloc(&s.d_norm, s.vec * sizeof(double)));
+  CK(cudaMalloc(&s.d_disc, 3 * (d + 1) * sizeof(double)));
+  CK(cudaMalloc(&s.d_ints, 4 * (d + 8) * sizeof(int)));
+  CK(cudaMalloc(&s.d_sync, sizeof(DevSync)));
+  CK(cudaMemsetAsync(s.d_sync, 0, sizeof(DevSync), ctx->stream));
+  CK(cudaMemsetAsync(s.d_disc, 0, 3 * (d + 1) * sizeof(double), ctx->stream));
+  s.phi = new Mps();
+  s.eta = new Mps();
+  s.theta = new Mps();
+  CKS(mps_alloc(ctx, c.phi, s.phi));
+  CKS(mps_alloc(ctx, c.eta, s.eta));
+  CKS(mps_alloc(ctx, c.theta, s.theta));
+  ctx->ws_nvmax = z.nvmax;
+  ctx->ws_ellmax = z.ellmax;
+  ctx->ws_ready = true;
+  return QTT_OK;
+}
+
+// Workspace for a step with MPO bonds w and c^2 ranks rc (grown if needed).
+qtt_status ensure_ws(qtt_ctx* ctx, const std::vector<int>& w, const std::vector<int>& rc) {
+  Caps c = step_caps(ctx, w, rc);
+  Sizes z = step_sizes(ctx, c, w, rc);
+  if (ctx->ws_ready) {
+    const Workspace& s = ctx->ws;
+    bool ok = s.tv >= z.tv && s.carry >= z.carry && s.xbuf >= z.x && s.rv >= z.rv && s.jv >= z.jv &&
+              s.w1 >= z.w1 && s.vec >= z.vec && ctx->ws_nvmax >= z.nvmax && s.theta->cap == c.theta &&
+              s.phi->cap == c.phi && s.eta->cap == c.eta;
+    if (ok) return QTT_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ws_free(ctx);
+  }
+  return ws_alloc(ctx, z, c);
+}
+
+// workspace for setup-only work (no MPO / c^2 known yet)
+qtt_status ensure_ws_basic(qtt_ctx* ctx) {
+  if (ctx->ws_ready) return QTT_OK;
+  std::vector<int> w(ctx->d + 1, 5), rc(ctx->d + 1, 1);
+  w[0] = w[ctx->d] = 1;
+  return ensure_ws(ctx, w, rc);
+}
+
+qtt_status device_status(qtt_ctx* ctx) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, &ctx->ws.d_sync->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st != 0) {
+    CK(cudaMemsetAsync(ctx->ws.d_sync, 0, sizeof(DevSync), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const char* what = st == QTT_ENOCONV ? "Jacobi SVD reached its sweep limit"
+                       : st == QTT_ETIMEOUT ? "a grid barrier wait timed out"
+                       : st == QTT_ENONFINITE ? "non-finite singular value"
+                                              : "device error";
+    return fail((qtt_status)st, what);
+  }
+  return QTT_OK;
+}
+
+// ------------------------------------------------------------- SVD helper
+// Truncated SVD of nv vectors (rows of the vector-major array Tv, ld ell,
+// not modified).  Jacobi rotations J satisfy: the rotated vectors
+// J^T Tv have orthogonal rows.  Writes the kept rank to rank_out and
+// Jp (r x nv) / Jt (nv x r).
+qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvmax, long long ellmax, double eps,
+                  int chi, int rank_cap, int* rank_out, double* Jp, double* Jt, double* disc_out,
+                  double* sigma_out);
+
+GemmArgs gemm0();
+
+}  // namespace
+
+namespace {
+
+// Truncated SVD of nv vectors (rows of the vector-major array Tv, ld ell,
+// not modified).  J (nv x r) holds the kept right singular vectors of the
+// matrix M whose columns are the vectors: M J = U S.  Writes the kept rank
+// to rank_out, Jp = J^T (r x nv) and Jt = J (nv x r).  The Jacobi sweeps
+// always run on a square problem of size min(nv, ell):
+//   ell >= nv: M = Q R, rotate the columns of R (Q never formed);
+//   ell <  nv: M^T = Q R, rotate the rows of R, J = Q J_R.
+qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvmax, long long ellmax, double eps,
+                  int chi, int rank_cap, int* rank_out, double* Jp, double* Jt, double* disc_out,
+                  double* sigma_out) {
+  Workspace& s = ctx->ws;
+  const long long ldv = ctx->ws_nvmax;  // R / J leading dimension
+  if (nvmax > ldv || ellmax * nvmax > s.tv)
+    return fail(QTT_EINVAL, "internal: SVD larger than the workspace");
+  double* sig = sigma_out ? sigma_out : s.d_sig;
+  int* kq = s.d_ints + 0;
+  if (ellmax >= nvmax) {
+    Dim len = ell;
+    if (ellmax > nvmax) {
+      // M (ell x nv, column i = vector i) = Q R;  R column-major with ld ldv
+      KL(KC_QR, qr_f64(ctx, Tv, ell, s.d_tq, ellmax, ell, nv, nvmax, s.d_rv, false, nullptr, kq, ldv, 0));
+      KL(KC_JACOBI, jacobi_f64(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, s.d_jv, ldv, s.d_norm));
+      len = dptr(kq);
+    } else {
+      KL(KC_COPY, copy2d(Tv, s.d_tq, nv, ell, ell, dconst(1), dconst(ellmax), dconst(1), nvmax * ellmax, 1.0,
+                ctx->stream));
+      KL(KC_JACOBI, jacobi_f64(ctx, s.d_tq, ellmax, nv, ell, nvmax, s.d_jv, ldv, s.d_norm));
+    }
+    KL(KC_POST, svd_post(ctx, s.d_norm, nv, len, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt));
+    return QTT_OK;
+  }
+  if (ellmax > ldv) return fail(QTT_EINVAL, "internal: SVD larger than the workspace");
+  // M^T (nv x ell): its columns are the ell components, stored contiguously
+  KL(KC_COPY, copy2d(Tv, s.d_tt, nv, ell, ell, dconst(1), dconst(1), dconst(nvmax), nvmax * ellmax, 1.0, ctx->stream));
+  KL(KC_QR, qr_f64(ctx, s.d_tt, dconst(nvmax), s.d_tq, nvmax, nv, ell, ellmax, s.d_rv, true, s.d_qt, kq, ellmax, nvmax));
+  // rows of R (kq x ell, ld ellmax) are the vectors of the reduced problem
+  KL(KC_JACOBI, jacobi_f64(ctx, s.d_rv, ellmax, dptr(kq), ell, ellmax, s.d_jh, ldv, s.d_norm));
+  // J_v[c][i] = sum_j J_R[c][j] Q[i][j]
+  GemmArgs g = gemm0();
+  g.A = s.d_jh;
+  g.B = s.d_qt;
+  g.C = s.d_jv;
+  g.M = dptr(kq);
+  g.N = nv;
+  g.K = dptr(kq);
+  g.sai = dconst(ldv);
+  g.sak = dconst(1);
+  g.sbk = dconst(1);
+  g.sbj = dptr(kq);
+  g.sci = dconst(ldv);
+  g.scj = dconst(1);
+  KL(KC_GEMM, gemm_f64(g, ellmax, nvmax, 1, 1, ctx->stream));
+  KL(KC_POST, svd_post(ctx, s.d_norm, dptr(kq), ell, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt));
+  return QTT_OK;
+}
+
+GemmArgs gemm0() {
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.nb1 = dconst(1);
+  g.nb2 = dconst(1);
+  g.sa1 = g.sa2 = g.sb1 = g.sb2 = g.sc1 = g.sc2 = dconst(0);
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  return g;
+}
+
+// ---------------------------------------------------------------- zip-ups
+// phi = L psi, sweeping sites 0 -> d-1 (with the carry of Eq. 9-12).
+qtt_status zipup_L(qtt_ctx* ctx, const Mpo* L, const Mps* psi, Mps* phi, const Caps& c) {
+  Workspace& s = ctx->ws;
+  const int d = ctx->d;
+  const double eps = ctx->p.eps_zip;
+  const int chi = ctx->p.chi_zip;
+  KL(KC_OTHER, init_zip(s.d_carry, phi->ranks, d, nullptr, nullptr, 0, ctx->stream));
+  for (int k = 0; k < d; ++k) {
+    const int w = L->w[k], w2 = L->w[k + 1];
+    const int* a_p = phi->ranks + k;
+    const int* b_p = psi->ranks + k;
+    const int* b2_p = psi->ranks + k + 1;
+    // X[(a,w)][(s,b')] = C[(a,w)][b] A_k[b][(s,b')]
+    GemmArgs g = gemm0();
+    g.A = s.d_carry;
+    g.B = psi->core(k);
+    g.C = s.d_x;
+    g.M = dptr(a_p, w);
+    g.N = dptr(b2_p, 2);
+    g.K = dptr(b_p);
+    g.sai = dptr(b_p);
+    g.sak = dconst(1);
+    g.sbk = dptr(b2_p, 2);
+    g.sbj = dconst(1);
+    g.sci = dptr(b2_p, 2);
+    g.scj = dconst(1);
+    KL(KC_GEMM, gemm_f64(g, (long long)c.phi[k] * w, 2LL * c.psi[k + 1], 1, 1, ctx->stream));
+    const double* Wk = L->data + L->off[k];
+    const long long tot = 2LL * c.phi[k] * w2 * c.psi[k + 1];
+    if (k == d - 1) {  // w' = b' = 1: T is the last core
+      KL(KC_MPO, mpo_apply_lr(s.d_x, phi->core(k), Wk, w, w2, a_p, b2_p, tot, ctx->stream));
+      break;
+    }
+    KL(KC_MPO, mpo_apply_lr(s.d_x, s.d_tv, Wk, w, w2, a_p, b2_p, tot, ctx->stream));
+    int* r_p = phi->ranks + k + 1;
+    const Dim nv = dptr(a_p, 2), ell = dptr(b2_p, w2);
+    CKS(svd_vm(ctx, s.d_tv, nv, ell, 2LL * c.phi[k], (long long)w2 * c.psi[k + 1], eps, chi, c.phi[k + 1], r_p,
+               s.d_jp, phi->core(k), s.d_disc + 0 * (d + 1) + k + 1, nullptr));
+    // carry C'[j][(w',b')] = sum_i Jp[j][i] T[i][(w',b')]
+    GemmArgs h = gemm0();
+    h.A = s.d_jp;
+    h.B = s.d_tv;
+    h.C = s.d_carry;
+    h.M = dptr(r_p);
+    h.N = ell;
+    h.K = nv;
+    h.sai = nv;
+    h.sak = dconst(1);
+    h.sbk = ell;
+    h.sbj = dconst(1);
+    h.sci = ell;
+    h.scj = dconst(1);
+    KL(KC_GEMM, gemm_f64(h, c.phi[k + 1], (long long)w2 * c.psi[k + 1], 1, 1, ctx->stream));
+  }
+  return QTT_OK;
+}
+
+// eta = C^2 phi, the diagonal MPO of the c^2 MPS, sweeping sites d-1 -> 0.
+qtt_status zipup_C(qtt_ctx* ctx, const Mps* c2, const std::vector<int>& rc, const Mps* phi, Mps* eta,
+                   const Caps& c) {
+  Workspace& s = ctx->ws;
+  const int d = ctx->d;
+  const double eps = ctx->p.eps_zip;
+  const int chi = ctx->p.chi_zip;
+  KL(KC_OTHER, init_zip(s.d_carry, eta->ranks, d, nullptr, nullptr, 0, ctx->stream));
+  for (int k = d - 1; k >= 0; --k) {
+    const int R = rc[k], R2 = rc[k + 1];
+    const int* B_p = phi->ranks + k;
+    const int* B2_p = phi->ranks + k + 1;
+    const int* A2_p = eta->ranks + k + 1;
+    // Z[t][b][(r',a')] = sum_b' phi_k[b][t][b'] C[b'][(r',a')]
+    GemmArgs g = gemm0();
+    g.A = phi->core(k);
+    g.B = s.d_carry;
+    g.C = s.d_x;
+    g.M = dptr(B_p);
+    g.N = dptr(A2_p, R2);
+    g.K = dptr(B2_p);
+    g.sai = dptr(B2_p, 2);
+    g.sak = dconst(1);
+    g.sbk = dptr(A2_p, R2);
+    g.sbj = dconst(1);
+    g.sci = dptr(A2_p, R2);
+    g.scj = dconst(1);
+    g.nb1 = dconst(2);
+    g.sa1 = dptr(B2_p);
+    g.sb1 = dconst(0);
+    g.sc1 = dptr2(B_p, A2_p, R2);
+    KL(KC_GEMM, gemm_f64(g, c.phi[k], (long long)R2 * c.eta[k + 1], 2, 1, ctx->stream));
+    // T[(t,a')][(b,r)] = sum_r' B_k[r][t][r'] Z[t][b][r'][a']
+    double* Tdst = (k == 0) ? eta->core(0) : s.d_tv;
+    GemmArgs h = gemm0();
+    h.A = c2->core(k);
+    h.B = s.d_x;
+    h.C = Tdst;
+    h.M = dconst(R);
+    h.N = dptr(A2_p);
+    h.K = dconst(R2);
+    h.sai = dconst(2LL * R2);
+    h.sak = dconst(1);
+    h.sbk = dptr(A2_p);
+    h.sbj = dconst(1);
+    h.sci = dconst(1);
+    h.scj = dptr(B_p, R);
+    h.nb1 = dconst(2);
+    h.nb2 = dptr(B_p);
+    h.sa1 = dconst(R2);
+    h.sa2 = dconst(0);
+    h.sb1 = dptr2(B_p, A2_p, R2);
+    h.sb2 = dptr(A2_p, R2);
+    h.sc1 = dptr2(A2_p, B_p, R);
+    h.sc2 = dconst(R);
+    KL(KC_GEMM, gemm_f64(h, R, c.eta[k + 1], 2, c.phi[k], ctx->stream));
+    if (k == 0) break;
+    int* r_p = eta->ranks + k;
+    const Dim nv = dptr(A2_p, 2), ell = dptr(B_p, R);
+    CKS(svd_vm(ctx, s.d_tv, nv, ell, 2LL * c.eta[k + 1], (long long)c.phi[k] * R, eps, chi, c.eta[k], r_p,
+               eta->core(k), nullptr, s.d_disc + 1 * (d + 1) + k, nullptr));
+    // carry C'[(b,r)][j] = sum_i T[i][(b,r)] Jp[j][i]  (Jp = eta core k)
+    GemmArgs q = gemm0();
+    q.A = s.d_tv;
+    q.B = eta->core(k);
+    q.C = s.d_carry;
+    q.M = ell;
+    q.N = dptr(r_p);
+    q.K = nv;
+    q.sai = dconst(1);
+    q.sak = ell;
+    q.sbk = dconst(1);
+    q.sbj = nv;
+    q.sci = dptr(r_p);
+    q.scj = dconst(1);
+    KL(KC_GEMM, gemm_f64(q, (long long)c.phi[k] * R, c.eta[k], 1, 1, ctx->stream));
+  }
+  return QTT_OK;
+}
+
+// -------------------------------------------------------------------- sum
+qtt_status form_sum(qtt_ctx* ctx, const std::vector<std::pair<double, const Mps*>>& terms, const long* src,
+                    double amp, Mps* out) {
+  const int d = ctx->d;
+  SumArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.d = d;
+  a.nterms = (int)terms.size();
+  for (int t = 0; t < a.nterms; ++t) {
+    a.coef[t] = terms[t].first;
+    a.ranks[t] = terms[t].second->ranks;
+    for (int k = 0; k < d; ++k) a.core[t][k] = terms[t].second->core(k);
+  }
+  for (int k = 0; k < d; ++k) a.out[k] = out->core(k);
+  a.out_ranks = out->ranks;
+  a.has_src = src ? 1 : 0;
+  a.src_amp = amp;
+  if (src) {
+    const int n = ctx->p.n;
+    for (int k = 0; k < d; ++k) {
+      long long v;
+      int b;
+      if (ctx->p.order == QTT_ORDER_SEQUENTIAL) {
+        v = k < n ? src[0] : src[1];
+        b = k < n ? k : k - n;
+      } else {
+        v = (k & 1) ? src[1] : src[0];
+        b = k >> 1;
+      }
+      a.src_bits[k] = (int)((v >> b) & 1);
+    }
+  }
+  long long mx = 1;
+  for (int k = 0; k < d; ++k) mx = std::max(mx, (long long)out->cap[k] * 2 * out->cap[k + 1]);
+  KL(KC_SUM, mps_sum(a, mx, ctx->stream));
+  return QTT_OK;
+}
+
+// ------------------------------------------------------------------ round
+// out = round(theta): QR sweep 0 -> d-1, then truncated-SVD sweep d-1 -> 1
+// (Sec. 4.3).  theta is overwritten.
+qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
+  Workspace& s = ctx->ws;
+  const int d = ctx->d;
+  const std::vector<int>& cap = th->cap;
+  int* Dsave = s.d_ints + 8;  // original theta ranks, d+1 ints
+  KL(KC_OTHER, init_zip(nullptr, out->ranks, d, th->ranks, Dsave, d + 1, ctx->stream));
+  // theta_0 (1 x 2 x D_1) -> vector-major columns: M[y][s]
+  KL(KC_COPY, copy2d(th->core(0), s.d_tv, dconst(2), dptr(Dsave + 1), dptr(Dsave + 1), dconst(1), dconst(1), dconst(2),
+            2LL * cap[1], 1.0, ctx->stream));
+  for (int k = 0; k < d - 1; ++k) {
+    int* q_p = th->ranks + k;       // q_k (rows / 2 of the matrix)
+    int* kq_p = th->ranks + k + 1;  // becomes min(2 q_k, D_{k+1})
+    const Dim m = dptr(q_p, 2), n = dptr(Dsave + k + 1);
+    const long long ldw = 2LL * cap[k];
+    KL(KC_QR, qr_f64(ctx, s.d_tv, m, s.d_tq, ldw, m, n, cap[k + 1], s.d_rv, true, th->core(k), kq_p, cap[k + 1], ldw));
+    // next core (kq x 2 x D_{k+2}) = R (kq x D_{k+1}) theta_{k+1}
+    GemmArgs g = gemm0();
+    g.A = s.d_rv;
+    g.B = th->core(k + 1);
+    g.C = s.d_tv;
+    g.M = dptr(kq_p);
+    g.N = dptr(Dsave + k + 2);
+    g.K = dptr(Dsave + k + 1);
+    g.sai = dconst(cap[k + 1]);
+    g.sak = dconst(1);
+    g.sbk = dptr(Dsave + k + 2, 2);
+    g.sbj = dconst(1);
+    g.nb1 = dconst(2);
+    g.sa1 = dconst(0);
+    g.sb1 = dptr(Dsave + k + 2);
+    if (k + 1 < d - 1) {  // QR layout: column y holds (x', s)
+      g.sci = dconst(2);
+      g.scj = dptr(kq_p, 2);
+      g.sc1 = dconst(1);
+    } else {  // SVD layout of the last core: vector s holds x'
+      g.sci = dconst(1);
+      g.scj = dptr(kq_p);
+      g.sc1 = dptr(kq_p);
+    }
+    KL(KC_GEMM, gemm_f64(g, std::min<long long>(2LL * cap[k], cap[k + 1]), cap[k + 2], 2, 1, ctx->stream));
+  }
+  for (int k = d - 1; k >= 1; --k) {
+    const int* q_p = th->ranks + k;  // rows of core k
+    const int* r2_p = out->ranks + k + 1;
+    int* r_p = out->ranks + k;
+    const Dim nv = dptr(r2_p, 2), ell = dptr(q_p);
+    const long long nvmax = 2LL * out->cap[k + 1];
+    const long long ellmax = std::min<long long>(cap[k], p2(k));  // q_k <= 2^k after the QR sweep
+    CKS(svd_vm(ctx, s.d_tv, nv, ell, nvmax, ellmax, ctx->p.eps, ctx->p.chi_max, out->cap[k], r_p, out->core(k),
+               nullptr, s.d_disc + 2 * (d + 1) + k, nullptr));
+    // W1 (r x q_k) = Jp Tv
+    GemmArgs g = gemm0();
+    g.A = out->core(k);
+    g.B = s.d_tv;
+    g.C = s.d_w1;
+    g.M = dptr(r_p);
+    g.N = ell;
+    g.K = nv;
+    g.sai = nv;
+    g.sak = dconst(1);
+    g.sbk = ell;
+    g.sbj = dconst(1);
+    g.sci = ell;
+    g.scj = dconst(1);
+    KL(KC_GEMM, gemm_f64(g, out->cap[k], cap[k], 1, 1, ctx->stream));
+    // core_{k-1} (q_{k-1} x 2 x r) = Q_{k-1} (q_{k-1} x 2 x q_k) W1^T
+    const int* ql_p = th->ranks + k - 1;
+    GemmArgs h = gemm0();
+    h.A = th->core(k - 1);
+    h.B = s.d_w1;
+    h.M = dptr(ql_p);
+    h.N = dptr(r_p);
+    h.K = dptr(q_p);
+    h.sai = dptr(q_p, 2);
+    h.sak = dconst(1);
+    h.sbk = dconst(1);
+    h.sbj = dptr(q_p);
+    h.nb1 = dconst(2);
+    h.sa1 = dptr(q_p);
+    h.sb1 = dconst(0);
+    if (k - 1 >= 1) {  // SVD layout for the next bond: vector (s', j) holds w
+      h.C = s.d_tv;
+      h.sci = dconst(1);
+      h.scj = dptr(ql_p);
+      h.sc1 = dptr2(r_p, ql_p);
+    } else {  // final core 0: [1][2][r]
+      h.C = out->core(0);
+      h.sci = dconst(0);
+      h.scj = dconst(1);
+      h.sc1 = dptr(r_p);
+    }
+    KL(KC_GEMM, gemm_f64(h, cap[k - 1], out->cap[k], 2, 1, ctx->stream));
+  }
+  return QTT_OK;
+}
+
+// ------------------------------------------------------------------ TT-SVD
+// MPS of a dense grid (site tensor built on the device), truncated (eps, chi).
+qtt_status tt_svd(qtt_ctx* ctx, const double* grid_dev, bool square, double eps, int chi, Mps* out) {
+  Workspace& s = ctx->ws;
+  const int d = ctx->d, n = ctx->p.n;
+  double* cur = s.d_carry;
+  double* nxt = s.d_x;
+  KL(KC_OTHER, site_permute(grid_dev, cur, n, ctx->p.order, square, ctx->stream));
+  KL(KC_OTHER, init_zip(nullptr, out->ranks, d, nullptr, nullptr, 0, ctx->stream));
+  for (int k = 0; k < d - 1; ++k) {
+    const long long ell = p2(d - k - 1);
+    const int* rl_p = out->ranks + k;
+    int* r_p = out->ranks + k + 1;
+    // rank of bond k is at most min(2^k, 2^(d-k), chi) whatever the buffer holds
+    const long long capk = std::min<long long>({(long long)out->cap[k], p2(k), p2(d - k), (long long)chi});
+    const long long capk1 = std::min<long long>({(long long)out->cap[k + 1], p2(k + 1), p2(d - k - 1), (long long)chi});
+    const long long nvmax = 2 * capk;
+    CKS(svd_vm(ctx, cur, dptr(rl_p, 2), dconst(ell), nvmax, ell, eps, chi, (int)capk1, r_p, s.d_jp, out->core(k),
+               nullptr, nullptr));
+    GemmArgs g = gemm0();
+    g.A = s.d_jp;
+    g.B = cur;
+    g.C = nxt;
+    g.M = dptr(r_p);
+    g.N = dconst(ell);
+    g.K = dptr(rl_p, 2);
+    g.sai = dptr(rl_p, 2);
+    g.sak = dconst(1);
+    g.sbk = dconst(ell);
+    g.sbj = dconst(1);
+    g.sci = dconst(ell);
+    g.scj = dconst(1);
+    KL(KC_GEMM, gemm_f64(g, capk1, ell, 1, 1, ctx->stream));
+    std::swap(cur, nxt);
+  }
+  // last core (r_{d-1} x 2 x 1) is the remainder
+  KL(KC_COPY, copy2d(cur, out->core(d - 1), dptr(out->ranks + d - 1, 2), dconst(1), dconst(1), dconst(1), dconst(1), dconst(1),
+            2LL * out->cap[d - 1], 1.0, ctx->stream));
+  return QTT_OK;
+}
+
+bool cuda_ok_device() {
+  int n = 0;
+  return cudaGetDeviceCount(&n) == cudaSuccess && n > 0;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+const char* qtt_last_error(void) { return g_err.c_str(); }
+
+qtt_status qtt_ctx_create(const qtt_params* p, void* stream, qtt_ctx** out) {
+  if (!p || !out) return fail(QTT_EINVAL, "null argument");
+  *out = nullptr;
+  if (p->n < 1 || p->n > 14) return fail(QTT_EINVAL, "n must be in 1..14");
+  if (p->order != QTT_ORDER_SEQUENTIAL && p->order != QTT_ORDER_INTERLEAVED) return fail(QTT_EINVAL, "bad order");
+  if (p->bc != QTT_BC_PERIODIC && p->bc != QTT_BC_ZERO) return fail(QTT_EINVAL, "bad boundary condition");
+  if (p->prec != QTT_FP64) return fail(QTT_EINVAL, "only the QTT_FP64 form is built in this library version");
+  if (p->chi_max < 1 || p->chi_max > 1024) return fail(QTT_EINVAL, "chi_max must be in 1..1024");
+  if (!(p->eps >= 0.0 && p->eps < 1.0)) return fail(QTT_EINVAL, "eps must be in [0, 1)");
+  if (p->chi_zip < 0 || p->chi_zip > 1024 || p->chi_c < 0 || p->chi_c > 1024)
+    return fail(QTT_EINVAL, "chi_zip / chi_c must be in 0..1024");
+  if (p->use_learned_rank != 0) return fail(QTT_EINVAL, "use_learned_rank is reserved");
+  if (!cuda_ok_device()) return fail(QTT_ECUDA, "no CUDA device");
+  qtt_ctx* c = new qtt_ctx();
+  c->p = *p;
+  if (c->p.chi_zip == 0) c->p.chi_zip = c->p.chi_max;
+  if (!(c->p.eps_zip > 0.0)) c->p.eps_zip = c->p.eps;
+  if (c->p.chi_c == 0) c->p.chi_c = c->p.chi_max;
+  if (!(c->p.eps_c > 0.0)) c->p.eps_c = 1e-8;
+  c->d = 2 * p->n;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = linalg_init(c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(QTT_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
+  }
+  c->coop_blocks = coop_max_blocks(c->num_sms);
+  *out = c;
+  return QTT_OK;
+}
+
+void qtt_ctx_destroy(qtt_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  ws_free(ctx);
+  for (auto& e : ctx->prof.ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (ctx->prof.d_log) cudaFree(ctx->prof.d_log);
+  delete ctx;
+}
+
+qtt_status qtt_ctx_sync(qtt_ctx* ctx) {
+  if (!ctx) return fail(QTT_EINVAL, "null context");
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->ws_ready) return QTT_OK;
+  return device_status(ctx);
+}
+
+qtt_status qtt_mps_create_zero(qtt_ctx* ctx, qtt_mps** out) {
+  if (!ctx || !out) return fail(QTT_EINVAL, "null argument");
+  qtt_mps* m = new qtt_mps();
+  qtt_status s = mps_alloc(ctx, psi_caps(ctx->d, ctx->p.chi_max), m);
+  if (s != QTT_OK) {
+    mps_free(m);
+    delete m;
+    return s;
+  }
+  *out = m;
+  return QTT_OK;
+}
+
+void qtt_mps_destroy(qtt_mps* m) {
+  if (!m) return;
+  if (m->ctx) cudaStreamSynchronize(m->ctx->stream);
+  mps_free(m);
+  delete m;
+}
+
+qtt_status qtt_mps_from_cores(qtt_ctx* ctx, const int* ranks, const double* cores, qtt_mps** out) {
+  if (!ctx || !ranks || !cores || !out) return fail(QTT_EINVAL, "null argument");
+  const int d = ctx->d;
+  std::vector<int> cap = psi_caps(d, ctx->p.chi_max);
+  if (ranks[0] != 1 || ranks[d] != 1) return fail(QTT_EINVAL, "ranks[0] and ranks[d] must be 1");
+  for (int k = 0; k <= d; ++k)
+    if (ranks[k] < 1 || ranks[k] > cap[k]) return fail(QTT_EINVAL, "rank outside 1..capacity");
+  qtt_mps* m = nullptr;
+  CKS(qtt_mps_create_zero(ctx, &m));
+  long long src = 0;
+  for (int k = 0; k < d; ++k) {
+    long long sz = (long long)ranks[k] * 2 * ranks[k + 1];
+    cudaError_t e = cudaMemcpyAsync(m->core(k), cores + src, sz * sizeof(double), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e != cudaSuccess) {
+      qtt_mps_destroy(m);
+      return fail(QTT_ECUDA, cudaGetErrorString(e));
+    }
+    src += sz;
+  }
+  CK(cudaMemcpyAsync(m->ranks, ranks, (d + 1) * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = m;
+  return QTT_OK;
+}
+
+qtt_status qtt_mps_ranks(qtt_ctx* ctx, const qtt_mps* psi, int* ranks_out) {
+  if (!ctx || !psi || !ranks_out) return fail(QTT_EINVAL, "null argument");
+  CK(cudaMemcpyAsync(ranks_out, psi->ranks, (psi->d + 1) * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->ws_ready) CKS(device_status(ctx));
+  return QTT_OK;
+}
+
+qtt_status qtt_mps_get_cores(qtt_ctx* ctx, const qtt_mps* psi, int* ranks, double* cores, long cap) {
+  CKS(qtt_mps_ranks(ctx, psi, ranks));
+  if (!cores) return QTT_OK;
+  long long need = 0;
+  for (int k = 0; k < psi->d; ++k) need += (long long)ranks[k] * 2 * ranks[k + 1];
+  if (need > cap) return fail(QTT_EINVAL, "cores buffer too small");
+  long long dst = 0;
+  for (int k = 0; k < psi->d; ++k) {
+    long long sz = (long long)ranks[k] * 2 * ranks[k + 1];
+    CK(cudaMemcpyAsync(cores + dst, psi->core(k), sz * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    dst += sz;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return QTT_OK;
+}
+
+static qtt_status from_dense_impl(qtt_ctx* ctx, const double* grid, int on_device, bool square, double eps, int chi,
+                                  qtt_mps** out) {
+  if (!ctx || !grid || !out) return fail(QTT_EINVAL, "null argument");
+  CKS(ensure_ws_basic(ctx));
+  const long long N2 = p2(2 * ctx->p.n);
+  const double* g = grid;
+  double* tmp = nullptr;
+  if (!on_device) {
+    CK(cudaMalloc(&tmp, N2 * sizeof(double)));
+    CK(cudaMemcpyAsync(tmp, grid, N2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    g = tmp;
+  }
+  qtt_mps* m = new qtt_mps();
+  qtt_status s = mps_alloc(ctx, psi_caps(ctx->d, chi), m);
+  if (square) {  // c^2: the TT-SVD itself, cores 0..d-2 left-orthonormal
+    if (s == QTT_OK) s = tt_svd(ctx, g, square, eps, chi, m);
+  } else {  // a state: TT-SVD, then the Sec. 4.3 round (right-orthonormal cores 1..d-1)
+    if (s == QTT_OK) s = tt_svd(ctx, g, square, eps, chi, ctx->ws.theta);
+    if (s == QTT_OK) s = tt_round(ctx, ctx->ws.theta, m);
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (tmp) cudaFree(tmp);
+  if (s == QTT_OK && e != cudaSuccess) s = fail(QTT_ECUDA, cudaGetErrorString(e));
+  if (s == QTT_OK) s = device_status(ctx);
+  if (s == QTT_OK) {
+    m->host_ranks.assign(ctx->d + 1, 1);
+    if (cudaMemcpy(m->host_ranks.data(), m->ranks, (ctx->d + 1) * sizeof(int), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      s = fail(QTT_ECUDA, "rank read-back");
+  }
+  if (s != QTT_OK) {
+    mps_free(m);
+    delete m;
+    return s;
+  }
+  *out = m;
+  return QTT_OK;
+}
+
+qtt_status qtt_mps_from_dense(qtt_ctx* ctx, const double* grid, int on_device, qtt_mps** out) {
+  if (!ctx) return fail(QTT_EINVAL, "null context");
+  CKS(ensure_ws_basic(ctx));
+  return from_dense_impl(ctx, grid, on_device, false, ctx->p.eps, ctx->p.chi_max, out);
+}
+
+qtt_status qtt_velocity_mps(qtt_ctx* ctx, const double* c_grid, int on_device, qtt_mps** c2_out) {
+  if (!ctx) return fail(QTT_EINVAL, "null context");
+  return from_dense_impl(ctx, c_grid, on_device, true, ctx->p.eps_c, ctx->p.chi_c, c2_out);
+}
+
+qtt_status qtt_laplacian_mpo(qtt_ctx* ctx, qtt_mpo** out) {
+  if (!ctx || !out) return fail(QTT_EINVAL, "null argument");
+  qtt_mpo* m = new qtt_mpo();
+  build_laplacian(ctx->p.n, ctx->p.order, ctx->p.bc, m);
+  cudaError_t e = cudaMalloc(&m->data, m->host.size() * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->data, m->host.data(), m->host.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (m->data) cudaFree(m->data);
+    delete m;
+    return fail(QTT_ECUDA, cudaGetErrorString(e));
+  }
+  *out = m;
+  return QTT_OK;
+}
+
+qtt_status qtt_mpo_bonds(const qtt_mpo* L, int* bonds_out) {
+  if (!L || !bonds_out) return fail(QTT_EINVAL, "null argument");
+  for (int k = 0; k <= L->d; ++k) bonds_out[k] = L->w[k];
+  return QTT_OK;
+}
+
+void qtt_mpo_destroy(qtt_mpo* L) {
+  if (!L) return;
+  if (L->data) cudaFree(L->data);
+  delete L;
+}
+
+qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, double amp) {
+  if (!ctx || !psi) return fail(QTT_EINVAL, "null argument");
+  const long N = 1L << ctx->p.n;
+  if (ix < 0 || ix >= N || iz < 0 || iz >= N) return fail(QTT_EINVAL, "source outside the grid");
+  CKS(ensure_ws_basic(ctx));
+  Workspace& s = ctx->ws;
+  // theta needs room for psi + 1
+  for (int k = 1; k < ctx->d; ++k)
+    if (s.theta->cap[k] < psi->cap[k] + 1) return fail(QTT_EINVAL, "internal: sum workspace too small");
+  long src[2] = {ix, iz};
+  CKS(form_sum(ctx, {{1.0, psi}}, src, amp, s.theta));
+  CKS(tt_round(ctx, s.theta, psi));
+  return QTT_OK;
+}
+
+qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* prev, qtt_mps* cur,
+                    const long* src, double amp) {
+  if (!ctx || !L || !c2 || !prev || !cur) return fail(QTT_EINVAL, "null argument");
+  if (L->d != ctx->d || c2->d != ctx->d || prev->d != ctx->d || cur->d != ctx->d)
+    return fail(QTT_EINVAL, "handle from another grid size");
+  if (prev == cur) return fail(QTT_EINVAL, "psi_prev and psi_cur must differ");
+  if (!(lambda2 >= 0.0) || !std::isfinite(lambda2)) return fail(QTT_EINVAL, "lambda2 must be finite, >= 0");
+  const long N = 1L << ctx->p.n;
+  if (src && (src[0] < 0 || src[0] >= N || src[1] < 0 || src[1] >= N))
+    return fail(QTT_EINVAL, "source outside the grid");
+  std::vector<int> rc = c2->cap;  // c^2 ranks are fixed; capacities bound them
+  if (c2->host_ranks.size() == (size_t)ctx->d + 1) rc = c2->host_ranks;
+  CKS(ensure_ws(ctx, L->w, rc));
+  Caps c = step_caps(ctx, L->w, rc);
+  Workspace& s = ctx->ws;
+  CKS(zipup_L(ctx, L, cur, s.phi, c));
+  CKS(zipup_C(ctx, c2, rc, s.phi, s.eta, c));
+  CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta));
+  CKS(tt_round(ctx, s.theta, prev));
+  // prev now holds u^{k+1}: exchange buffers so that prev = u^k, cur = u^{k+1}
+  std::swap(prev->data, cur->data);
+  std::swap(prev->ranks, cur->ranks);
+  return QTT_OK;
+}
+
+qtt_status qtt_sample(qtt_ctx* ctx, const qtt_mps* psi, const long* ix, const long* iz, long count, double* out) {
+  if (!ctx || !psi || (count > 0 && (!ix || !iz || !out))) return fail(QTT_EINVAL, "null argument");
+  if (count < 0) return fail(QTT_EINVAL, "negative count");
+  if (count == 0) return QTT_OK;
+  SampleArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.d = ctx->d;
+  a.n = ctx->p.n;
+  a.order = ctx->p.order;
+  a.rmax = *std::max_element(psi->cap.begin(), psi->cap.end());
+  for (int k = 0; k < ctx->d; ++k) a.core[k] = psi->core(k);
+  a.ranks = psi->ranks;
+  a.ix = ix;
+  a.iz = iz;
+  a.count = count;
+  a.out = out;
+  KL(KC_OTHER, sample(a, ctx->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_to_dense(qtt_ctx* ctx, const qtt_mps* psi, double* out) {
+  if (!ctx || !psi || !out) return fail(QTT_EINVAL, "null argument");
+  CKS(ensure_ws_basic(ctx));
+  Workspace& s = ctx->ws;
+  const int d = ctx->d, h = d / 2;
+  const long long nL = p2(h), nR = p2(d - h);
+  const int rmax = *std::max_element(psi->cap.begin(), psi->cap.end());
+  const long long rh = psi->cap[h];
+  if (nL * rh > s.xbuf || rh * nR > s.carry || nL * nR > s.tv) return fail(QTT_EINVAL, "internal: to_dense scratch");
+  ChainArgs l, r;
+  std::memset(&l, 0, sizeof(l));
+  l.d = d;
+  l.h = h;
+  l.rmax = rmax;
+  for (int k = 0; k < d; ++k) l.core[k] = psi->core(k);
+  l.ranks = psi->ranks;
+  r = l;
+  l.out = s.d_x;      // Lm: nL x r_h
+  r.out = s.d_carry;  // Rm: r_h x nR
+  KL2(KC_OTHER, chains(l, r, ctx->stream));
+  GemmArgs g = gemm0();
+  g.A = s.d_x;
+  g.B = s.d_carry;
+  g.C = s.d_tv;
+  g.M = dconst(nL);
+  g.N = dconst(nR);
+  g.K = dptr(psi->ranks + h);
+  g.sai = dptr(psi->ranks + h);
+  g.sak = dconst(1);
+  g.sbk = dconst(nR);
+  g.sbj = dconst(1);
+  g.sci = dconst(nR);
+  g.scj = dconst(1);
+  KL(KC_GEMM, gemm_f64(g, nL, nR, 1, 1, ctx->stream));
+  KL(KC_OTHER, scatter_dense(s.d_tv, out, ctx->p.n, ctx->p.order, h, ctx->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_svd_trunc(qtt_ctx* ctx, const double* M, int m, int n, double eps, int chi, double* U, double* S,
+                         double* Vt, int* rank_out) {
+  if (!ctx || !M || !U || !S || !Vt || !rank_out) return fail(QTT_EINVAL, "null argument");
+  if (m < 1 || n < 1) return fail(QTT_EINVAL, "empty matrix");
+  if (!(eps >= 0.0)) return fail(QTT_EINVAL, "eps must be >= 0");
+  CKS(ensure_ws_basic(ctx));
+  Workspace& s = ctx->ws;
+  const long long nv = std::min(m, n), ell = std::max(m, n);
+  if (nv > ctx->ws_nvmax || nv * ell > s.tv || ell > ctx->ws_ellmax * 64)
+    return fail(QTT_EINVAL, "matrix larger than the context workspace");
+  int* r_d = s.d_ints + 4;
+  const int chic = chi <= 0 ? (int)nv : chi;
+  if (m <= n) {
+    // vectors = rows of M; U = J (m x r), Vt = S^-1 Jp M
+    CKS(svd_vm(ctx, M, dconst(m), dconst(n), m, n, eps, chic, (int)nv, r_d, s.d_jp, U, nullptr, S));
+    GemmArgs g = gemm0();
+    g.A = s.d_jp;
+    g.B = M;
+    g.C = Vt;
+    g.M = dptr(r_d);
+    g.N = dconst(n);
+    g.K = dconst(m);
+    g.sai = dconst(m);
+    g.sak = dconst(1);
+    g.sbk = dconst(n);
+    g.sbj = dconst(1);
+    g.sci = dconst(n);
+    g.scj = dconst(1);
+    KL(KC_GEMM, gemm_f64(g, nv, n, 1, 1, ctx->stream));
+    KL(KC_OTHER, scale_rows(Vt, n, dconst(n), r_d, S, nv * n, ctx->stream));
+  } else {
+    // vectors = columns of M (copied vector-major); Vt = Jp; U = (M J) S^-1
+    KL(KC_COPY, copy2d(M, s.d_tv, dconst(m), dconst(n), dconst(n), dconst(1), dconst(1), dconst(m), (long long)m * n, 1.0,
+              ctx->stream));
+    CKS(svd_vm(ctx, s.d_tv, dconst(n), dconst(m), n, m, eps, chic, (int)nv, r_d, Vt, nullptr, nullptr, S));
+    GemmArgs g = gemm0();  // W = Jp Mv  (r x m) into jp scratch
+    g.A = Vt;
+    g.B = s.d_tv;
+    g.C = s.d_w1;
+    g.M = dptr(r_d);
+    g.N = dconst(m);
+    g.K = dconst(n);
+    g.sai = dconst(n);
+    g.sak = dconst(1);
+    g.sbk = dconst(m);
+    g.sbj = dconst(1);
+    g.sci = dconst(m);
+    g.scj = dconst(1);
+    if ((long long)nv * m > s.w1) return fail(QTT_EINVAL, "matrix larger than the context workspace");
+    KL(KC_GEMM, gemm_f64(g, nv, m, 1, 1, ctx->stream));
+    KL(KC_OTHER, scale_rows(s.d_w1, m, dconst(m), r_d, S, nv * m, ctx->stream));
+    // U[i][j] = W[j][i]
+    KL(KC_COPY, copy2d(s.d_w1, U, dptr(r_d), dconst(m), dconst(m), dconst(1), dconst(1), dptr(r_d), nv * m, 1.0,
+              ctx->stream));
+  }
+  CK(cudaMemcpyAsync(rank_out, r_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return device_status(ctx);
+}
+
+qtt_status qtt_fdtd_step(qtt_ctx* ctx, const double* c2, double lambda2, const double* up, const double* uc,
+                         double* un, long sx, long sz, double amp) {
+  if (!ctx || !c2 || !up || !uc || !un) return fail(QTT_EINVAL, "null argument");
+  const long N = 1L << ctx->p.n;
+  if (sx >= N || sz < 0 || sz >= N) sx = -1;
+  KL(KC_FDTD, fdtd(c2, lambda2, up, uc, un, ctx->p.n, ctx->p.bc, sx, sz, amp, ctx->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_profile_start(qtt_ctx* ctx, int timing, int log_svd) {
+  if (!ctx) return fail(QTT_EINVAL, "null context");
+  Prof& p = ctx->prof;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int c = 0; c < KC_N; ++c) p.launches[c] = 0;
+  p.used = 0;
+  p.timing = timing ? 1 : 0;
+  p.log_used = 0;
+  if (log_svd) {
+    if (!p.d_log) {
+      p.log_cap = 65536;
+      CK(cudaMalloc(&p.d_log, 2 * p.log_cap * sizeof(int)));
+    }
+  } else if (p.d_log) {
+    cudaFree(p.d_log);
+    p.d_log = nullptr;
+    p.log_cap = 0;
+  }
+  return QTT_OK;
+}
+
+qtt_status qtt_profile_read(qtt_ctx* ctx, qtt_profile* out) {
+  if (!ctx || !out) return fail(QTT_EINVAL, "null argument");
+  Prof& p = ctx->prof;
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::memset(out, 0, sizeof(*out));
+  for (int c = 0; c < KC_N && c < QTT_KCLASSES; ++c) out->launches[c] = p.launches[c];
+  for (int i = 0; i < p.used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p.ev[i].first, p.ev[i].second));
+    out->ms[p.cls[i]] += ms;
+  }
+  if (p.d_log && p.log_used > 0) {
+    std::vector<int> h(2 * p.log_used);
+    CK(cudaMemcpy(h.data(), p.d_log, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    double f = 0.0;
+    for (int i = 0; i < p.log_used; ++i) {
+      double a = h[2 * i], b = h[2 * i + 1];
+      double n = std::min(a, b), m = std::max(a, b);
+      f += 6.0 * m * n * n + 20.0 * n * n * n;
+    }
+    out->svd_logged = p.log_used;
+    out->svd_flops = f;
+  }
+  return device_status(ctx);
+}
+
+qtt_status qtt_last_step_discarded(qtt_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(QTT_EINVAL, "null argument");
+  if (!ctx->ws_ready) return fail(QTT_EINVAL, "no step has run");
+  const int d = ctx->d;
+  std::vector<double> h(3 * (d + 1));
+  CK(cudaMemcpyAsync(h.data(), ctx->ws.d_disc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int ph = 0; ph < 3; ++ph)
+    for (int b = 1; b < d; ++b) out[ph * (d - 1) + b - 1] = h[ph * (d + 1) + b];
+  return device_status(ctx);
+}
+
+}  // extern "C"

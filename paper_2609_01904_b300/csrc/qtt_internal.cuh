@@ -1,0 +1,253 @@
+// Internal declarations of the QTT stepper library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda/atomic>
+
+#include <cstdint>
+#include <utility>
+#include <string>
+#include <vector>
+
+#include "../../include/qtt.h"
+
+namespace qtt {
+
+// ---------------------------------------------------------------------------
+// Device-side dimensions.  Bond ranks change every step and live in device
+// memory, so kernels evaluate their sizes and strides on the device:
+//   value = add + mul * (p1 ? *p1 : 1) * (p2 ? *p2 : 1)
+// A pure constant has mul = 0.  The host sizes grids from capacities.
+// ---------------------------------------------------------------------------
+struct Dim {
+  const int* p1;
+  const int* p2;
+  long long mul;
+  long long add;
+};
+
+inline Dim dconst(long long v) { return Dim{nullptr, nullptr, 0, v}; }
+inline Dim dptr(const int* p, long long mul = 1, long long add = 0) { return Dim{p, nullptr, mul, add}; }
+inline Dim dptr2(const int* p, const int* q, long long mul = 1, long long add = 0) {
+  return Dim{p, q, mul, add};
+}
+
+__device__ __forceinline__ long long dv(const Dim& d) {
+  long long v = d.mul;
+  if (d.mul != 0) {
+    if (d.p1) v *= (long long)(*d.p1);
+    if (d.p2) v *= (long long)(*d.p2);
+  }
+  return d.add + v;
+}
+
+// ---------------------------------------------------------------------------
+// Device status word and grid barrier with bounded waits.  A wait that runs
+// out records QTT_ETIMEOUT and returns false; the kernel then unwinds.
+// ---------------------------------------------------------------------------
+struct DevSync {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int counters[4];
+  int status;
+  int pad[9];
+};
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_status(DevSync* s, int code) {
+  atomicCAS(&s->status, 0, code);
+}
+
+// All CTAs of a cooperative launch call this the same number of times.
+__device__ __forceinline__ bool grid_sync(DevSync* s) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(s->bar_gen);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(s->bar_count);
+    cuda::atomic_ref<int, cuda::thread_scope_device> st(s->status);
+    unsigned int g = gen.load(cuda::memory_order_acquire);
+    unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+    int ok = 1;
+    if (arrived == nb - 1) {
+      cnt.store(0u, cuda::memory_order_relaxed);
+      gen.fetch_add(1u, cuda::memory_order_release);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      while (gen.load(cuda::memory_order_acquire) == g) {
+        if (st.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          set_status(s, QTT_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    if (st.load(cuda::memory_order_relaxed) != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ double block_sum(double v, double* red /* >= 32 */) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  if (w == 0) {
+    double t = (l < nw) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) red[0] = t;
+  }
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+struct Mps {
+  qtt_ctx* ctx = nullptr;
+  int d = 0;
+  std::vector<int> cap;        // capacity of bonds 0..d
+  std::vector<long long> off;  // element offset of core k in data (capacity layout)
+  long long total = 0;         // capacity in doubles
+  double* data = nullptr;      // device
+  int* ranks = nullptr;        // device, d+1
+  std::vector<int> host_ranks; // host copy when the ranks are fixed (c^2)
+  double* core(int k) const { return data + off[k]; }
+};
+
+struct Mpo {
+  int d = 0;
+  std::vector<int> w;           // bonds 0..d
+  std::vector<long long> off;   // offset of core k
+  std::vector<double> host;     // cores, [w_k][2][2][w_{k+1}]
+  double* data = nullptr;       // device copy
+};
+
+}  // namespace qtt
+
+struct qtt_mps : qtt::Mps {};
+struct qtt_mpo : qtt::Mpo {};
+
+namespace qtt {
+
+// Workspace: every scratch buffer of the step, sized from capacities once.
+struct Workspace {
+  long long carry = 0, xbuf = 0, tv = 0, tq = 0, rv = 0, jv = 0, jp = 0, w1 = 0, vec = 0;
+  double* d_carry = nullptr;  // zip-up carried tensor
+  double* d_x = nullptr;      // contraction intermediate
+  double* d_tv = nullptr;     // SVD input: nv vectors (vector-major)
+  double* d_tq = nullptr;     // QR working copy
+  double* d_rv = nullptr;     // R factor, vector-major (nv vectors)
+  double* d_jv = nullptr;     // Jacobi rotations, vector-major (nv x nv)
+  double* d_jp = nullptr;     // kept rotations, row-major (r x nv)
+  double* d_w1 = nullptr;     // absorption intermediate
+  double* d_tt = nullptr;     // transposed vectors (wide SVDs)
+  double* d_qt = nullptr;     // thin Q of a wide SVD
+  double* d_jh = nullptr;     // Jacobi rotations of the reduced problem
+  double* d_tau = nullptr;    // Householder scalars
+  double* d_sig = nullptr;    // singular values (sorted)
+  double* d_norm = nullptr;   // vector norms from the Jacobi sweeps
+  double* d_disc = nullptr;   // discarded weights per (phase, bond)
+  int* d_ints = nullptr;      // scratch ints (ranks of temporaries)
+  DevSync* d_sync = nullptr;
+  Mps* phi = nullptr;
+  Mps* eta = nullptr;
+  Mps* theta = nullptr;
+  Mps* spare = nullptr;
+};
+
+}  // namespace qtt
+
+namespace qtt {
+enum { KC_GEMM = 0, KC_QR, KC_JACOBI, KC_POST, KC_MPO, KC_SUM, KC_COPY, KC_FDTD, KC_OTHER, KC_N };
+
+struct Prof {
+  int timing = 0;
+  int used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  std::vector<int> cls;
+  long long launches[KC_N] = {0};
+  int* d_log = nullptr;     // (nv, m) of each Jacobi launch while profiling
+  int log_cap = 0;
+  int log_used = 0;
+};
+}  // namespace qtt
+
+struct qtt_ctx {
+  qtt_params p{};
+  int d = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int coop_blocks = 0;  // co-resident CTAs for the cooperative kernels
+  qtt::Workspace ws;
+  bool ws_ready = false;
+  qtt::Prof prof;
+  long long ws_nvmax = 0;   // widest SVD (vectors) the workspace holds
+  long long ws_ellmax = 0;  // longest vector of a step SVD
+};
+
+namespace qtt {
+
+// ---------------------------------------------------------------- kernels
+// (defined in the .cu files; all launch on ctx->stream)
+
+struct GemmArgs {
+  const double* A;
+  const double* B;
+  double* C;
+  Dim M, N, K;
+  Dim sai, sak, sbk, sbj, sci, scj;  // element strides
+  Dim nb1, nb2;                      // two-level batch counts
+  Dim sa1, sa2, sb1, sb2, sc1, sc2;  // batch strides
+  double alpha, beta;
+};
+// C[b1,b2](i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j); Mmax/Nmax/nbmax size the grid.
+cudaError_t gemm_f64(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max,
+                     long long nb2max, cudaStream_t st);
+
+// Householder QR of the m x n matrix whose column j is Ain + j*lda (length m).
+// R (kq x n, kq = min(m,n)) is written to Rout row-major (R[i][c] at i*ldr+c)
+// if r_rowmajor else column-major (c*ldr+i); Q (m x kq) row-major to Qout if
+// not null; kq to *kq_out if not null.  Work: column j at W + j*ldw.
+// ldr: leading dimension of a column-major R.  Q formation needs m <= qm_max
+// (the column is built in shared memory).
+cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n,
+                   long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
+                   long long qm_max = 0);
+
+// One-sided Jacobi on nv vectors V + i*ldv of length m; J (nv x nv,
+// vector-major, ld ldj) accumulates the rotations; norms[i] = |v_i| at the end.
+cudaError_t jacobi_f64(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, double* J,
+                       long long ldj, double* norms);
+int* jacobi_log_slot(qtt_ctx* ctx);
+
+// Sort, truncate, write rank, sigma, discarded weight and the kept rotations:
+// Jp[j*nv + i] = J[perm_j][i] (j < r), and Jt[i*r + j] the same if Jt != null.
+// cnt rotated vectors with norms; len: their length (min(cnt, len) singular
+// values exist); jlen: length of a row of J (the number of input vectors);
+// rank_cap: the destination capacity (a larger rank is clamped and reported).
+cudaError_t svd_post(qtt_ctx* ctx, const double* norms, Dim cnt, Dim len, Dim jlen, const double* J, long long ldj,
+                     double eps, int chi, int rank_cap, int* rank_out, double* sigma_out, double* disc_out,
+                     double* Jp, double* Jt);
+
+}  // namespace qtt

@@ -1,0 +1,328 @@
+"""ctypes binding of the C ABI in include/qtt.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: device buffers are torch CUDA tensors (float64 /
+int64, contiguous) passed by pointer, handles are opaque wrappers.  A missing
+or unloadable ``libqtt.so`` raises at import; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqtt.so")
+
+QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENOCONV, QTT_ETIMEOUT, QTT_ENONFINITE = range(7)
+ORDERS = {"sequential": 0, "interleaved": 1}
+BCS = {"periodic": 0, "zero": 1}
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
+STATUS_NAMES = {0: "QTT_OK", 1: "QTT_EINVAL", 2: "QTT_ENOMEM", 3: "QTT_ECUDA", 4: "QTT_ENOCONV",
+                5: "QTT_ETIMEOUT", 6: "QTT_ENONFINITE"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2609_01904_b300.build`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class qtt_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("order", ctypes.c_int), ("bc", ctypes.c_int), ("prec", ctypes.c_int),
+                ("chi_max", ctypes.c_int), ("eps", ctypes.c_double), ("chi_zip", ctypes.c_int),
+                ("eps_zip", ctypes.c_double), ("chi_c", ctypes.c_int), ("eps_c", ctypes.c_double),
+                ("use_learned_rank", ctypes.c_int)]
+
+
+class QttError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.qtt_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_long
+_D = ctypes.c_double
+_PI = ctypes.POINTER(ctypes.c_int)
+_PD = ctypes.POINTER(ctypes.c_double)
+_PL = ctypes.POINTER(ctypes.c_long)
+
+QTT_KCLASSES = 9
+KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "copy", "fdtd", "other"]
+
+
+class qtt_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_long * QTT_KCLASSES), ("ms", ctypes.c_double * QTT_KCLASSES),
+                ("svd_logged", ctypes.c_long), ("svd_flops", ctypes.c_double)]
+
+
+_SIGS = {
+    "qtt_ctx_create": [ctypes.POINTER(qtt_params), _P, ctypes.POINTER(_P)],
+    "qtt_ctx_sync": [_P],
+    "qtt_mps_create_zero": [_P, ctypes.POINTER(_P)],
+    "qtt_mps_from_dense": [_P, _P, _I, ctypes.POINTER(_P)],
+    "qtt_mps_from_cores": [_P, _PI, _PD, ctypes.POINTER(_P)],
+    "qtt_mps_get_cores": [_P, _P, _PI, _PD, _L],
+    "qtt_mps_ranks": [_P, _P, _PI],
+    "qtt_velocity_mps": [_P, _P, _I, ctypes.POINTER(_P)],
+    "qtt_laplacian_mpo": [_P, ctypes.POINTER(_P)],
+    "qtt_mpo_bonds": [_P, _PI],
+    "qtt_inject_source": [_P, _P, _L, _L, _D],
+    "qtt_step": [_P, _P, _P, _D, _P, _P, _PL, _D],
+    "qtt_sample": [_P, _P, _P, _P, _L, _P],
+    "qtt_to_dense": [_P, _P, _P],
+    "qtt_svd_trunc": [_P, _P, _I, _I, _D, _I, _P, _P, _P, _PI],
+    "qtt_fdtd_step": [_P, _P, _D, _P, _P, _P, _L, _L, _D],
+    "qtt_last_step_discarded": [_P, _PD],
+    "qtt_profile_start": [_P, _I, _I],
+    "qtt_profile_read": [_P, ctypes.POINTER(qtt_profile)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+for _name in ("qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy"):
+    getattr(_lib, _name).argtypes = [_P]
+    getattr(_lib, _name).restype = None
+_lib.qtt_last_error.argtypes = []
+_lib.qtt_last_error.restype = ctypes.c_char_p
+
+# every symbol include/qtt.h declares
+EXPORTED = sorted(list(_SIGS) + ["qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_last_error"])
+
+
+def _check(st: int, where: str) -> None:
+    if st != QTT_OK:
+        raise QttError(st, where)
+
+
+def _dev_ptr(t, dtype_name: str = "float64") -> int:
+    import torch
+    want = {"float64": torch.float64, "int64": torch.int64}[dtype_name]
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != want or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous CUDA {dtype_name} tensor")
+    return t.data_ptr()
+
+
+class Ctx:
+    def __init__(self, handle: int, params: qtt_params):
+        self.h = handle
+        self.params = params
+
+    @property
+    def n(self) -> int:
+        return self.params.n
+
+    @property
+    def d(self) -> int:
+        return 2 * self.params.n
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qtt_ctx_destroy(self.h)
+            self.h = None
+
+
+class Mps:
+    def __init__(self, handle: int, ctx: Ctx):
+        self.h = handle
+        self.ctx = ctx
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qtt_mps_destroy(self.h)
+            self.h = None
+
+
+class Mpo:
+    def __init__(self, handle: int, ctx: Ctx):
+        self.h = handle
+        self.ctx = ctx
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qtt_mpo_destroy(self.h)
+            self.h = None
+
+
+def qtt_last_error() -> str:
+    return _lib.qtt_last_error().decode(errors="replace")
+
+
+def qtt_ctx_create(n: int, order: str = "interleaved", bc: str = "periodic", chi_max: int = 32,
+                   eps: float = 1e-10, chi_zip: int = 0, eps_zip: float = 0.0, chi_c: int = 0,
+                   eps_c: float = 0.0, prec: str = "fp64", stream=None) -> Ctx:
+    """Context on the current CUDA device; ``stream`` is a torch.cuda.Stream
+    (default: torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, chi_zip, eps_zip, chi_c, eps_c, 0)
+    h = _P()
+    _check(_lib.qtt_ctx_create(ctypes.byref(p), _P(stream.cuda_stream), ctypes.byref(h)), "qtt_ctx_create")
+    return Ctx(h.value, p)
+
+
+def qtt_ctx_destroy(ctx: Ctx) -> None:
+    if ctx.h:
+        _lib.qtt_ctx_destroy(ctx.h)
+        ctx.h = None
+
+
+def qtt_mps_destroy(psi: Mps) -> None:
+    if psi.h:
+        _lib.qtt_mps_destroy(psi.h)
+        psi.h = None
+
+
+def qtt_mpo_destroy(L: Mpo) -> None:
+    if L.h:
+        _lib.qtt_mpo_destroy(L.h)
+        L.h = None
+
+
+def qtt_ctx_sync(ctx: Ctx) -> None:
+    _check(_lib.qtt_ctx_sync(ctx.h), "qtt_ctx_sync")
+
+
+def qtt_mps_create_zero(ctx: Ctx) -> Mps:
+    h = _P()
+    _check(_lib.qtt_mps_create_zero(ctx.h, ctypes.byref(h)), "qtt_mps_create_zero")
+    return Mps(h.value, ctx)
+
+
+def qtt_mps_from_dense(ctx: Ctx, grid) -> Mps:
+    """grid: CUDA float64 tensor (N, N) or a host numpy array."""
+    h = _P()
+    ptr, on_dev, keep = _grid_arg(grid)
+    _check(_lib.qtt_mps_from_dense(ctx.h, _P(ptr), on_dev, ctypes.byref(h)), "qtt_mps_from_dense")
+    del keep
+    return Mps(h.value, ctx)
+
+
+def qtt_velocity_mps(ctx: Ctx, c_grid) -> Mps:
+    h = _P()
+    ptr, on_dev, keep = _grid_arg(c_grid)
+    _check(_lib.qtt_velocity_mps(ctx.h, _P(ptr), on_dev, ctypes.byref(h)), "qtt_velocity_mps")
+    del keep
+    return Mps(h.value, ctx)
+
+
+def _grid_arg(g):
+    import numpy as np
+    if isinstance(g, np.ndarray):
+        a = np.ascontiguousarray(g, dtype=np.float64)
+        return a.ctypes.data, 0, a
+    return _dev_ptr(g), 1, g
+
+
+def qtt_mps_from_cores(ctx: Ctx, cores) -> Mps:
+    """cores: list of d host arrays [r_k][2][r_{k+1}]."""
+    import numpy as np
+    ranks = [1] + [int(c.shape[2]) for c in cores]
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).ravel() for c in cores]))
+    r = (ctypes.c_int * len(ranks))(*ranks)
+    h = _P()
+    _check(_lib.qtt_mps_from_cores(ctx.h, r, flat.ctypes.data_as(_PD), ctypes.byref(h)), "qtt_mps_from_cores")
+    return Mps(h.value, ctx)
+
+
+def qtt_mps_ranks(psi: Mps) -> list[int]:
+    r = (ctypes.c_int * (psi.ctx.d + 1))()
+    _check(_lib.qtt_mps_ranks(psi.ctx.h, psi.h, r), "qtt_mps_ranks")
+    return list(r)
+
+
+def qtt_mps_get_cores(psi: Mps):
+    """Host copy of the cores as a list of numpy arrays."""
+    import numpy as np
+    ranks = qtt_mps_ranks(psi)
+    d = psi.ctx.d
+    tot = sum(ranks[k] * 2 * ranks[k + 1] for k in range(d))
+    buf = np.empty(max(tot, 1), dtype=np.float64)
+    r = (ctypes.c_int * (d + 1))()
+    _check(_lib.qtt_mps_get_cores(psi.ctx.h, psi.h, r, buf.ctypes.data_as(_PD), tot), "qtt_mps_get_cores")
+    out, o = [], 0
+    for k in range(d):
+        sz = ranks[k] * 2 * ranks[k + 1]
+        out.append(buf[o:o + sz].reshape(ranks[k], 2, ranks[k + 1]).copy())
+        o += sz
+    return out
+
+
+def qtt_laplacian_mpo(ctx: Ctx) -> Mpo:
+    h = _P()
+    _check(_lib.qtt_laplacian_mpo(ctx.h, ctypes.byref(h)), "qtt_laplacian_mpo")
+    return Mpo(h.value, ctx)
+
+
+def qtt_mpo_bonds(L: Mpo) -> list[int]:
+    b = (ctypes.c_int * (L.ctx.d + 1))()
+    _check(_lib.qtt_mpo_bonds(L.h, b), "qtt_mpo_bonds")
+    return list(b)
+
+
+def qtt_inject_source(psi: Mps, ix: int, iz: int, amp: float) -> None:
+    _check(_lib.qtt_inject_source(psi.ctx.h, psi.h, ix, iz, amp), "qtt_inject_source")
+
+
+def qtt_step(L: Mpo, c2: Mps, lambda2: float, psi_prev: Mps, psi_cur: Mps, src=None, amp: float = 0.0) -> None:
+    """Eq. 17: on return psi_prev holds u^k and psi_cur holds u^{k+1}."""
+    s = None
+    if src is not None:
+        s = (ctypes.c_long * 2)(int(src[0]), int(src[1]))
+    _check(_lib.qtt_step(psi_cur.ctx.h, L.h, c2.h, lambda2, psi_prev.h, psi_cur.h, s, amp), "qtt_step")
+
+
+def qtt_sample(psi: Mps, ix, iz, out) -> None:
+    """ix, iz: CUDA int64 tensors; out: CUDA float64 tensor of the same length."""
+    n = ix.numel()
+    _check(_lib.qtt_sample(psi.ctx.h, psi.h, _P(_dev_ptr(ix, "int64")), _P(_dev_ptr(iz, "int64")), n,
+                           _P(_dev_ptr(out))), "qtt_sample")
+
+
+def qtt_to_dense(psi: Mps, out) -> None:
+    """out: CUDA float64 tensor (N, N)."""
+    _check(_lib.qtt_to_dense(psi.ctx.h, psi.h, _P(_dev_ptr(out))), "qtt_to_dense")
+
+
+def qtt_svd_trunc(ctx: Ctx, M, eps: float, chi: int = 0):
+    """Truncated SVD of a CUDA float64 matrix (m, n): returns (U, S, Vt, r)."""
+    import torch
+    m, n = M.shape
+    k = min(m, n)
+    U = torch.zeros((m, k), dtype=torch.float64, device=M.device)
+    S = torch.zeros((k,), dtype=torch.float64, device=M.device)
+    Vt = torch.zeros((k, n), dtype=torch.float64, device=M.device)
+    r = ctypes.c_int(0)
+    _check(_lib.qtt_svd_trunc(ctx.h, _P(_dev_ptr(M)), m, n, eps, chi, _P(U.data_ptr()), _P(S.data_ptr()),
+                              _P(Vt.data_ptr()), ctypes.byref(r)), "qtt_svd_trunc")
+    r = r.value
+    return U.view(-1)[: m * r].view(m, r), S[:r], Vt[:r], r
+
+
+def qtt_fdtd_step(ctx: Ctx, c2, lambda2: float, u_prev, u_cur, u_next, src=None, amp: float = 0.0) -> None:
+    sx, sz = (-1, -1) if src is None else (int(src[0]), int(src[1]))
+    _check(_lib.qtt_fdtd_step(ctx.h, _P(_dev_ptr(c2)), lambda2, _P(_dev_ptr(u_prev)), _P(_dev_ptr(u_cur)),
+                              _P(_dev_ptr(u_next)), sx, sz, amp), "qtt_fdtd_step")
+
+
+def qtt_last_step_discarded(ctx: Ctx):
+    import numpy as np
+    out = np.zeros(3 * (ctx.d - 1))
+    _check(_lib.qtt_last_step_discarded(ctx.h, out.ctypes.data_as(_PD)), "qtt_last_step_discarded")
+    return out.reshape(3, ctx.d - 1)
+
+
+def qtt_profile_start(ctx: Ctx, timing: bool = False, log_svd: bool = False) -> None:
+    _check(_lib.qtt_profile_start(ctx.h, int(timing), int(log_svd)), "qtt_profile_start")
+
+
+def qtt_profile_read(ctx: Ctx) -> dict:
+    p = qtt_profile()
+    _check(_lib.qtt_profile_read(ctx.h, ctypes.byref(p)), "qtt_profile_read")
+    return {"launches": dict(zip(KERNEL_CLASSES, list(p.launches))), "ms": dict(zip(KERNEL_CLASSES, list(p.ms))),
+            "svd_logged": p.svd_logged, "svd_flops": p.svd_flops}
+
+
+__all__ = [n for n in EXPORTED] + ["Ctx", "Mps", "Mpo", "QttError", "qtt_params", "EXPORTED", "LIB_PATH"]

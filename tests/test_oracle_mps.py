@@ -196,11 +196,13 @@ def test_eigenmode_follows_cosine_recurrence(bc, order):
     L = O.laplacian_mpo(n, order, bc)
     cur = O.mps_from_dense(u0, n, order, 1e-14, 8)
     prev = O.mps_from_dense(ct * u0, n, order, 1e-14, 8)
-    for k in range(1, 121):
-        prev, cur = cur, O.mps_step(L, C, lam2c2, prev, cur, 1e-13, 16)
+    # cutoff 1e-11: above the rounding floor of the zip-up intermediates, far
+    # below the four exact Schmidt values of the mode
+    for k in range(1, 301):
+        prev, cur = cur, O.mps_step(L, C, lam2c2, prev, cur, 1e-11, 16)
         assert max(O.mps_ranks(cur)) <= 4
     got = O.mps_to_dense(cur, n, order)
-    np.testing.assert_allclose(got, math.cos(120 * th) * u0, atol=1e-10)
+    np.testing.assert_allclose(got, math.cos(300 * th) * u0, atol=5e-12)
 
 
 @pytest.mark.parametrize("order", ORDERS)
