@@ -175,6 +175,26 @@ qtt_status qtt_to_dense(qtt_ctx* ctx, const qtt_mps* psi, double* out_dev);
 qtt_status qtt_svd_trunc(qtt_ctx* ctx, const double* M_dev, int m, int n, double eps, int chi,
                          double* U_dev, double* S_dev, double* Vt_dev, int* rank_out);
 
+/* Truncated SVD with the same arithmetic and outputs as qtt_svd_trunc, for
+ * callers that cannot allocate device memory: code whose device memory is
+ * owned by another allocator (a framework's caching pool, an arena sized at
+ * start-up) and latency-critical loops that cannot take the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It needs no context and calls no
+ * allocator: its scratch is one file-scope device array of about 3.2 MB,
+ * present on every GPU that loads the library until the process exits.
+ * The paper has no counterpart of this call.
+ *   M_dev: m x n row-major device matrix (not modified); U_dev (m x min(m,n)),
+ *   S_dev (min(m,n)), Vt_dev (min(m,n) x n): device outputs laid out as for
+ *   qtt_svd_trunc; *rank_out: kept rank (host).  cuda_stream: cudaStream_t
+ *   (NULL = legacy default stream); the call synchronises it.
+ * Limits: max(m,n) <= 512 and min(m,n) <= 128, else QTT_EINVAL (message in
+ * qtt_last_error).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array: calls whose work overlaps on the GPU
+ * (two streams, two threads) race and corrupt each other's results. */
+qtt_status qtt_svd_trunc_noalloc(const double* M_dev, int m, int n, double eps, int chi, double* U_dev,
+                                 double* S_dev, double* Vt_dev, int* rank_out, void* cuda_stream);
+
 /* ------------------------------------------------------------- context */
 
 /* Dense FDTD update of Eq. 2 on the device (the scheme the MPS step

@@ -27,6 +27,14 @@ qtt_status fail(qtt_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+namespace qtt {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace qtt
+
+namespace {
+
 #define CK(call)                                                                               \
   do {                                                                                         \
     cudaError_t e_ = (call);                                                                   \

@@ -72,6 +72,7 @@ _SIGS = {
     "qtt_sample": [_P, _P, _P, _P, _L, _P],
     "qtt_to_dense": [_P, _P, _P],
     "qtt_svd_trunc": [_P, _P, _I, _I, _D, _I, _P, _P, _P, _PI],
+    "qtt_svd_trunc_noalloc": [_P, _I, _I, _D, _I, _P, _P, _P, _PI, _P],
     "qtt_fdtd_step": [_P, _P, _D, _P, _P, _P, _L, _L, _D],
     "qtt_last_step_discarded": [_P, _PD],
     "qtt_profile_start": [_P, _I, _I],
@@ -299,6 +300,21 @@ def qtt_svd_trunc(ctx: Ctx, M, eps: float, chi: int = 0):
                               _P(Vt.data_ptr()), ctypes.byref(r)), "qtt_svd_trunc")
     r = r.value
     return U.view(-1)[: m * r].view(m, r), S[:r], Vt[:r], r
+
+
+def qtt_svd_trunc_noalloc(M, U, S, Vt, eps: float, chi: int = 0, stream=None) -> int:
+    """The no-allocation truncated SVD: every buffer (CUDA float64, shapes
+    (m, n), (m, k), (k,), (k, n) with k = min(m, n)) is the caller's.
+    Returns the kept rank."""
+    import torch
+    m, n = M.shape
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    r = ctypes.c_int(0)
+    _check(_lib.qtt_svd_trunc_noalloc(_P(_dev_ptr(M)), m, n, eps, chi, _P(_dev_ptr(U)), _P(_dev_ptr(S)),
+                                      _P(_dev_ptr(Vt)), ctypes.byref(r), _P(stream.cuda_stream)),
+           "qtt_svd_trunc_noalloc")
+    return r.value
 
 
 def qtt_fdtd_step(ctx: Ctx, c2, lambda2: float, u_prev, u_cur, u_next, src=None, amp: float = 0.0) -> None:
