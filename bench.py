@@ -139,7 +139,7 @@ def run_ours(args, rank, world, local_rank):
     amps = wl.source_amplitudes(c, total)
     stream = torch.cuda.Stream()
     ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
-                           eps_c=wl.eps_c, prec="fp64", stream=stream)
+                           eps_c=wl.eps_c, prec=args.form, stream=stream)
     t0 = time.time()
     C, L, prev, cur = _setup_gpu_state(q, wl, ctx, c, amps, stream)
     setup_s = time.time() - t0
@@ -214,7 +214,8 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 of the recipe (1.25 TFLOP/s); FP64 FMA probe measured 0.95",
                 "work": "6 m n^2 + 20 n^3 per SVD of the reduced n x m problem (Golub-Van Loan)",
-                "launches": launches["jacobi"], "avg_launch_ms": ms["jacobi"] / max(launches["jacobi"], 1)}
+                "launches": launches["jacobi"], "avg_launch_ms": ms["jacobi"] / max(launches["jacobi"], 1),
+                "avg_sweeps": prof["svd_sweeps"] / max(prof["svd_logged"], 1)}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": None, "traffic": None}
@@ -233,10 +234,10 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if args.form == "fp64" else "f32+f64",
         "data": "synthetic (seeded Marmousi-shaped velocity section; Ricker source)",
         "config": {"workload": wl.name, "n": wl.n, "grid": f"{wl.N}x{wl.N}", "chi_max": wl.chi, "eps": wl.eps,
-                   "chi_c": wl.chi_c, "eps_c": wl.eps_c, "order": wl.order, "bc": wl.bc, "form": "fp64",
+                   "chi_c": wl.chi_c, "eps_c": wl.eps_c, "order": wl.order, "bc": wl.bc, "form": args.form,
                    "state": f"mid-run (step {MID_RUN} of {wl.steps})", "ranks_start": ranks0,
                    "ranks_end": ranks1, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}", "grid_point_updates_per_s": value * wl.N * wl.N,
@@ -345,6 +346,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

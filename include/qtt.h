@@ -60,7 +60,10 @@ typedef enum { QTT_FP64 = 0, QTT_TF32 = 1, QTT_BF16 = 2, QTT_FP32 = 3 } qtt_prec
  * qtt_bc; PERIODIC is the cyclic shift |x> -> |(x+1) mod 2^n> of Sec. 3.1 and
  * Sec. 4.2, ZERO is the terminal tensor of Eq. 11 as printed (the overflow is
  * dropped, i.e. u = 0 outside the grid).  prec: arithmetic of the
- * contractions (qtt_precision; QTT_FP64 is the plain form).  chi_max, eps:
+ * contractions (qtt_precision): QTT_FP64 is the plain form; QTT_FP32 runs
+ * the contractions and QR updates in FP32 and the truncation SVD of each
+ * bond factor as an FP32 Jacobi refined to FP64 accuracy in FP64 (the
+ * singular values, the rank decision and the discarded weight are FP64).  chi_max, eps:
  * truncation of the state (Sec. 4.3).  chi_zip, eps_zip: truncation inside
  * the two zip-up applications (0 = use chi_max / eps).  chi_c, eps_c:
  * truncation of the c^2 MPS (the paper does not say; 0 = chi_max / 1e-8).
@@ -215,8 +218,9 @@ qtt_status qtt_last_step_discarded(qtt_ctx* ctx, double* discarded);
 
 /* Kernel classes counted by qtt_profile: 0 GEMM contraction, 1 Householder
  * QR, 2 Jacobi SVD, 3 sort/truncate (Sec. 4.3 rule), 4 MPO application,
- * 5 MPS sum, 6 copy/transpose, 7 dense FDTD, 8 other. */
-#define QTT_KCLASSES 9
+ * 5 MPS sum, 6 copy/transpose, 7 dense FDTD, 8 FP64 refinement of the
+ * mixed-precision SVD, 9 other. */
+#define QTT_KCLASSES 10
 
 typedef struct {
   long launches[QTT_KCLASSES]; /* kernels launched since qtt_profile_start */
@@ -224,6 +228,8 @@ typedef struct {
   long svd_logged;             /* Jacobi launches whose size was logged */
   double svd_flops;            /* sum of 6 m n^2 + 20 n^3 over them (n <= m:
                                   the two sizes of the rotated problem) */
+  long svd_sweeps;             /* Jacobi sweeps over them (the last one finds
+                                  no pair to rotate) */
 } qtt_profile;
 
 /* Reset the counters of the context.  timing != 0 brackets every launch with

@@ -17,6 +17,7 @@ namespace qtt {
 namespace {
 
 constexpr int NT = 256;
+constexpr int kRegE = 2;  // register-resident Jacobi pairs up to NT * kRegE = 512 elements
 
 __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red /* 96 */) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -43,55 +44,101 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
 }
 
 // --------------------------------------------------------------------- QR
-__global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, Dim lda_d, double* W, long long ldw,
-                                                Dim m_d, Dim n_d, double* tau, double* Rout, int r_rowmajor,
-                                                long long ldr, double* Qout, int* kq_out, DevSync* sync) {
-  __shared__ double red[32];
-  extern __shared__ double ysh[];
+// Column c belongs to CTA c % G for the whole factorisation.  Reflector j is
+// formed by the owner of column j and published through flag[j]; a CTA
+// applies reflector j to its columns as soon as the flag is set.  The owner
+// of column j+1 applies reflector j to that column first and then forms
+// reflector j+1 (lookahead), so the critical path per column is one flag
+// hand-over plus one apply and one formation.
+template <typename T>
+__device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ void qr_form(T* x, long long j, long long m, T* tau, T* red) {
+  const int tid = threadIdx.x;
+  T s = T(0);
+  for (long long i = j + 1 + tid; i < m; i += NT) s = fma(x[i], x[i], s);
+  s = block_sum(s, red);
+  const T alpha = x[j];
+  T tj = T(0), beta = alpha;
+  if (s != T(0)) {
+    const T nrm = sqrt_t(alpha * alpha + s);
+    beta = alpha >= T(0) ? -nrm : nrm;
+    tj = (beta - alpha) / beta;
+    const T sc = T(1) / (alpha - beta);
+    for (long long i = j + 1 + tid; i < m; i += NT) x[i] *= sc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    x[j] = beta;
+    tau[j] = tj;
+  }
+}
+
+// y <- (I - tau v v^T) y on rows j..m-1 (v_j = 1 implicit); v is another CTA's
+// column, read through L2
+template <typename T>
+__device__ __forceinline__ void qr_apply(const T* v, T tj, T* y, long long j, long long m, T* red) {
+  const int tid = threadIdx.x;
+  T s = T(0);
+  for (long long i = j + 1 + tid; i < m; i += NT) s = fma(__ldcg(v + i), y[i], s);
+  s = block_sum(s, red);
+  const T w = tj * (y[j] + s);
+  if (tid == 0) y[j] -= w;
+  for (long long i = j + 1 + tid; i < m; i += NT) y[i] = fma(-w, __ldcg(v + i), y[i]);
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, Dim lda_d, T* W, long long ldw,
+                                                Dim m_d, Dim n_d, T* tau, double* Rout, int r_rowmajor,
+                                                long long ldr, double* Qout, int* kq_out, int* flag,
+                                                DevSync* sync) {
+  __shared__ T red[32];
+  __shared__ int s_ok;
+  extern __shared__ unsigned char ysh_raw[];
+  T* ysh = reinterpret_cast<T*>(ysh_raw);
   const long long m = dv(m_d), n = dv(n_d), lda = dv(lda_d);
   const long long kq = m < n ? m : n;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
 
   for (long long c = b; c < n; c += G)
-    for (long long i = tid; i < m; i += NT) W[c * ldw + i] = Ain[c * lda + i];
-  __syncthreads();
+    for (long long i = tid; i < m; i += NT) W[c * ldw + i] = T(Ain[c * lda + i]);
+  for (long long j = (long long)b * NT + tid; j < kq; j += (long long)G * NT) flag[j] = 0;
+  if (!grid_sync(sync)) return;
 
+  if (kq > 0 && b == 0) {  // column 0 is owned by CTA 0
+    qr_form(W, 0, m, tau, red);
+    if (tid == 0) {
+      __threadfence();
+      st_release(flag + 0, 1);
+    }
+  }
   for (long long j = 0; j < kq; ++j) {
-    if (j % G == b) {
-      double* x = W + j * ldw;
-      double s = 0.0;
-      for (long long i = j + 1 + tid; i < m; i += NT) s = fma(x[i], x[i], s);
-      s = block_sum(s, red);
-      const double alpha = x[j];
-      double tj = 0.0, beta = alpha;
-      if (s != 0.0) {
-        double nrm = sqrt(alpha * alpha + s);
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        tj = (beta - alpha) / beta;
-        double sc = 1.0 / (alpha - beta);
-        for (long long i = j + 1 + tid; i < m; i += NT) x[i] *= sc;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        x[j] = beta;
-        tau[j] = tj;
+    // last owned column: nothing left to apply once j reaches it
+    const long long last_owned = b + ((n - 1 - b) / G) * G;
+    if (b >= n || last_owned <= j) break;
+    if (tid == 0) s_ok = (j % G == b) ? 1 : (wait_geq(flag + j, 1, sync) ? 1 : 0);
+    __syncthreads();
+    if (!s_ok) return;
+    const T tj = __ldcg(tau + j);
+    const T* v = W + j * ldw;
+    const long long nx = j + 1;
+    if (nx < n && nx % G == b) {
+      T* y = W + nx * ldw;
+      if (tj != T(0)) qr_apply(v, tj, y, j, m, red);
+      if (nx < kq) {
+        qr_form(y, nx, m, tau, red);
+        if (tid == 0) {
+          __threadfence();
+          st_release(flag + nx, 1);
+        }
       }
     }
-    if (!grid_sync(sync)) return;
-    const double tj = tau[j];
-    if (tj == 0.0) continue;
-    const double* v = W + j * ldw;
-    long long c0 = b + ((j + 1 - b + G - 1) / G) * G;  // first owned column > j
-    if (j + 1 <= b) c0 = b;
-    for (long long c = c0; c < n; c += G) {
-      double* y = W + c * ldw;
-      double s = 0.0;
-      for (long long i = j + 1 + tid; i < m; i += NT) s = fma(v[i], y[i], s);
-      s = block_sum(s, red);
-      const double w = tj * (y[j] + s);
-      __syncthreads();
-      if (tid == 0) y[j] -= w;
-      for (long long i = j + 1 + tid; i < m; i += NT) y[i] = fma(-w, v[i], y[i]);
+    if (tj != T(0)) {
+      long long c0 = b + ((j + 2 - b + G - 1) / G) * G;  // first owned column > j+1
+      if (j + 2 <= b) c0 = b;
+      for (long long c = c0; c < n; c += G) qr_apply(v, tj, W + c * ldw, j, m, red);
     }
   }
   __syncthreads();
@@ -99,32 +146,34 @@ __global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, 
   // R: rows 0..kq-1 of the owned columns
   for (long long c = b; c < n; c += G) {
     for (long long i = tid; i < kq; i += NT) {
-      double r = i <= c ? W[c * ldw + i] : 0.0;
+      const double r = i <= c ? (double)W[c * ldw + i] : 0.0;
       if (r_rowmajor) Rout[i * ldr + c] = r;
       else Rout[c * ldr + i] = r;
     }
   }
   if (kq_out && b == 0 && tid == 0) *kq_out = (int)kq;
-  if (!Qout) return;
+  if (!Qout || kq == 0) return;
 
   // thin Q (m x kq, row-major): column c = H_0 ... H_c e_c, built in shared memory
+  if (tid == 0) s_ok = wait_geq(flag + kq - 1, 1, sync) ? 1 : 0;
+  __syncthreads();
+  if (!s_ok) return;
   for (long long c = b; c < kq; c += G) {
-    for (long long i = tid; i < m; i += NT) ysh[i] = (i == c) ? 1.0 : 0.0;
+    for (long long i = tid; i < m; i += NT) ysh[i] = (i == c) ? T(1) : T(0);
     __syncthreads();
     for (long long i = c; i >= 0; --i) {
-      const double ti = tau[i];
-      if (ti == 0.0) continue;
-      const double* v = W + i * ldw;
-      double s = 0.0;
-      for (long long l = i + 1 + tid; l < m; l += NT) s = fma(v[l], ysh[l], s);
+      const T ti = __ldcg(tau + i);
+      if (ti == T(0)) continue;
+      const T* v = W + i * ldw;
+      T s = T(0);
+      for (long long l = i + 1 + tid; l < m; l += NT) s = fma(__ldcg(v + l), ysh[l], s);
       s = block_sum(s, red);
-      const double w = ti * (ysh[i] + s);
-      __syncthreads();
+      const T w = ti * (ysh[i] + s);
       if (tid == 0) ysh[i] -= w;
-      for (long long l = i + 1 + tid; l < m; l += NT) ysh[l] = fma(-w, v[l], ysh[l]);
+      for (long long l = i + 1 + tid; l < m; l += NT) ysh[l] = fma(-w, __ldcg(v + l), ysh[l]);
       __syncthreads();
     }
-    for (long long i = tid; i < m; i += NT) Qout[i * kq + c] = ysh[i];
+    for (long long i = tid; i < m; i += NT) Qout[i * kq + c] = (double)ysh[i];
     __syncthreads();
   }
 }
@@ -141,23 +190,26 @@ __device__ __forceinline__ void circle_pair(long long rd, long long q, long long
   }
 }
 
+// Pairs follow the circle schedule; column c carries ver[c], the number of
+// rounds it has been through.  The CTA rotating (i, j) in global round t waits
+// until both columns reached t and then publishes t+1: no grid barrier per
+// round, only the two predecessors.  At the end of a sweep every CTA adds its
+// rotation count and waits for the others; a sweep without rotations ends it.
 __global__ void __launch_bounds__(NT) jacobi_kernel(double* V, long long ldv, Dim nv_d, Dim m_d, double* J,
                                                     long long ldj, double* norms, DevSync* sync, int max_sweeps,
-                                                    double tol, double tol_abs, int* log) {
+                                                    double tol, double tol_abs, int* log, int* ver) {
   __shared__ double red[96];
+  __shared__ int s_ok, s_total;
   const long long nv = dv(nv_d), m = dv(m_d);
-  if (log && blockIdx.x == 0 && threadIdx.x == 0) {
-    log[0] = (int)nv;
-    log[1] = (int)m;
-  }
   const long long P = nv + (nv & 1);
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
 
   for (long long c = b; c < nv; c += G)
     for (long long i = tid; i < nv; i += NT) J[c * ldj + i] = (i == c) ? 1.0 : 0.0;
-  if (b == 0 && tid == 0) {
-    sync->counters[0] = 0;
-    sync->counters[1] = 0;
+  for (long long c = (long long)b * NT + tid; c < P; c += (long long)G * NT) ver[c] = 0;
+  if (b == 0 && tid < 4) {
+    sync->counters[tid] = 0;
+    sync->done[tid] = 0;
   }
   if (!grid_sync(sync)) return;
 
@@ -166,57 +218,122 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* V, long long ldv, Di
     for (sweep = 0; sweep < max_sweeps; ++sweep) {
       int local = 0;
       for (long long rd = 0; rd < P - 1; ++rd) {
+        const int t = (int)(sweep * (P - 1) + rd);
         for (long long q = b; q < P / 2; q += G) {
           long long i, j;
           circle_pair(rd, q, P, i, j);
-          if (i >= nv || j >= nv) continue;
-          double* vi = V + i * ldv;
-          double* vj = V + j * ldv;
-          double a = 0.0, bb = 0.0, g = 0.0;
-          for (long long l = tid; l < m; l += NT) {
-            double x = vi[l], y = vj[l];
-            a = fma(x, x, a);
-            bb = fma(y, y, bb);
-            g = fma(x, y, g);
-          }
-          block_sum3(a, bb, g, red);
-          // rotate unless the pair is orthogonal to working precision, measured
-          // against both vectors and against the larger one alone (a pair whose
-          // norms differ by more than 1/tol cannot be made more orthogonal)
-          if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(bb) && fabs(g) > tol_abs * fmax(a, bb)) {
-            const double zeta = (bb - a) / (2.0 * g);
-            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-            for (long long l = tid; l < m; l += NT) {
-              double x = vi[l], y = vj[l];
-              vi[l] = cs * x - sn * y;
-              vj[l] = sn * x + cs * y;
-            }
+          if (tid == 0) s_ok = (wait_geq(ver + i, t, sync) && wait_geq(ver + j, t, sync)) ? 1 : 0;
+          __syncthreads();
+          if (!s_ok) return;
+          if (i < nv && j < nv) {
+            double* vi = V + i * ldv;
+            double* vj = V + j * ldv;
             double* Ji = J + i * ldj;
             double* Jj = J + j * ldj;
-            for (long long l = tid; l < nv; l += NT) {
-              double x = Ji[l], y = Jj[l];
-              Ji[l] = cs * x - sn * y;
-              Jj[l] = sn * x + cs * y;
+            if (m <= NT * kRegE && nv <= NT * kRegE) {
+              // one L2 pass: the pair and its rotation columns live in registers
+              double x[kRegE], y[kRegE], jx[kRegE], jy[kRegE];
+              double a = 0.0, bb = 0.0, g = 0.0;
+#pragma unroll
+              for (int e = 0; e < kRegE; ++e) {
+                const long long l = tid + (long long)e * NT;
+                x[e] = l < m ? __ldcg(vi + l) : 0.0;
+                y[e] = l < m ? __ldcg(vj + l) : 0.0;
+                jx[e] = l < nv ? __ldcg(Ji + l) : 0.0;
+                jy[e] = l < nv ? __ldcg(Jj + l) : 0.0;
+                a = fma(x[e], x[e], a);
+                bb = fma(y[e], y[e], bb);
+                g = fma(x[e], y[e], g);
+              }
+              block_sum3(a, bb, g, red);
+              // rotate unless the pair is orthogonal to working precision, measured
+              // against both vectors and against the larger one alone (a pair whose
+              // norms differ by more than 1/tol cannot be made more orthogonal)
+              if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(bb) && fabs(g) > tol_abs * fmax(a, bb)) {
+                const double zeta = (bb - a) / (2.0 * g);
+                const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+#pragma unroll
+                for (int e = 0; e < kRegE; ++e) {
+                  const long long l = tid + (long long)e * NT;
+                  if (l < m) {
+                    vi[l] = cs * x[e] - sn * y[e];
+                    vj[l] = sn * x[e] + cs * y[e];
+                  }
+                  if (l < nv) {
+                    Ji[l] = cs * jx[e] - sn * jy[e];
+                    Jj[l] = sn * jx[e] + cs * jy[e];
+                  }
+                }
+                ++local;
+              }
+            } else {
+              double a = 0.0, bb = 0.0, g = 0.0;
+              for (long long l = tid; l < m; l += NT) {
+                const double x = __ldcg(vi + l), y = __ldcg(vj + l);
+                a = fma(x, x, a);
+                bb = fma(y, y, bb);
+                g = fma(x, y, g);
+              }
+              block_sum3(a, bb, g, red);
+              if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(bb) && fabs(g) > tol_abs * fmax(a, bb)) {
+                const double zeta = (bb - a) / (2.0 * g);
+                const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+                for (long long l = tid; l < m; l += NT) {
+                  const double x = __ldcg(vi + l), y = __ldcg(vj + l);
+                  vi[l] = cs * x - sn * y;
+                  vj[l] = sn * x + cs * y;
+                }
+                for (long long l = tid; l < nv; l += NT) {
+                  const double x = __ldcg(Ji + l), y = __ldcg(Jj + l);
+                  Ji[l] = cs * x - sn * y;
+                  Jj[l] = sn * x + cs * y;
+                }
+                ++local;
+              }
             }
-            ++local;
+          }
+          __syncthreads();
+          if (tid == 0) {  // publish the CTA's writes (bar.sync, then fence + release)
+            __threadfence();
+            st_release(ver + i, t + 1);
+            st_release(ver + j, t + 1);
           }
         }
-        if (!grid_sync(sync)) return;
-        if (rd == 0 && b == 0 && tid == 0) sync->counters[(sweep + 1) & 1] = 0;
       }
-      if (tid == 0 && local) atomicAdd(&sync->counters[sweep & 1], local);
-      if (!grid_sync(sync)) return;
-      int total = *(volatile int*)&sync->counters[sweep & 1];
-      if (total == 0) break;
+      // end of sweep: total rotations over all CTAs
+      const int slot = sweep & 3;
+      if (tid == 0) {
+        if (local) atomicAdd(&sync->counters[slot], local);
+        __threadfence();
+        atomicAdd(&sync->done[slot], 1);
+        s_ok = wait_geq(&sync->done[slot], G, sync) ? 1 : 0;
+        s_total = ld_acquire(&sync->counters[slot]);
+        if (b == 0) {  // slot of sweep+2 is free: every CTA has read sweep-2's
+          sync->counters[(sweep + 2) & 3] = 0;
+          sync->done[(sweep + 2) & 3] = 0;
+        }
+      }
+      __syncthreads();
+      if (!s_ok) return;
+      if (s_total == 0) break;
     }
     if (sweep >= max_sweeps && b == 0 && tid == 0) set_status(sync, QTT_ENOCONV);
+  }
+  if (log && b == 0 && tid == 0) {
+    log[0] = (int)nv;
+    log[1] = (int)m;
+    log[2] = sweep + 1;
   }
   // final norms
   for (long long c = b; c < nv; c += G) {
     const double* vc = V + c * ldv;
     double s = 0.0;
-    for (long long l = tid; l < m; l += NT) s = fma(vc[l], vc[l], s);
+    for (long long l = tid; l < m; l += NT) {
+      const double x = __ldcg(vc + l);
+      s = fma(x, x, s);
+    }
     s = block_sum(s, red);
     if (tid == 0) norms[c] = sqrt(s);
   }
@@ -295,18 +412,33 @@ static cudaError_t coop_launch(const void* fn, int grid, int block, void** args,
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
-cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
-                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
+template <typename T>
+static cudaError_t qr_launch(qtt_ctx* ctx, const double* Ain, Dim lda, double* Wd, long long ldw, Dim m, Dim n,
+                             long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
+                             long long qm_max) {
   int grid = (int)std::min<long long>(ctx->coop_blocks, std::max<long long>(nmax, 1));
   size_t smem = 0;
-  if (Qout) smem = (size_t)qm_max * sizeof(double);
+  if (Qout) smem = (size_t)qm_max * sizeof(T);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  double* tau = ctx->ws.d_tau;
+  T* W = reinterpret_cast<T*>(Wd);
+  T* tau = reinterpret_cast<T*>(ctx->ws.d_tau);
   int rrm = r_rowmajor ? 1 : 0;
   DevSync* sync = ctx->ws.d_sync;
+  int* flag = ctx->ws.d_flags;
   void* args[] = {(void*)&Ain, (void*)&lda, (void*)&W, (void*)&ldw, (void*)&m, (void*)&n, (void*)&tau,
-                  (void*)&Rout, (void*)&rrm, (void*)&ldr, (void*)&Qout, (void*)&kq_out, (void*)&sync};
-  return coop_launch((const void*)qr_kernel, grid, NT, args, smem, ctx->stream);
+                  (void*)&Rout, (void*)&rrm, (void*)&ldr, (void*)&Qout, (void*)&kq_out, (void*)&flag,
+                  (void*)&sync};
+  return coop_launch((const void*)qr_kernel<T>, grid, NT, args, smem, ctx->stream);
+}
+
+cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
+                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
+  return qr_launch<double>(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max);
+}
+
+cudaError_t qr_f32(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
+                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
+  return qr_launch<float>(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max);
 }
 
 cudaError_t jacobi_f64(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, double* J,
@@ -319,8 +451,9 @@ cudaError_t jacobi_f64(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lo
   // rounding floor of accumulated rotations) or <= 1e-15 max(|v_i|^2, |v_j|^2)
   double tol = 1e-13, tol_abs = 1e-15;
   int* log = jacobi_log_slot(ctx);
+  int* ver = ctx->ws.d_flags;
   void* args[] = {(void*)&V, (void*)&ldv, (void*)&nv, (void*)&m, (void*)&J, (void*)&ldj, (void*)&norms,
-                  (void*)&sync, (void*)&max_sweeps, (void*)&tol, (void*)&tol_abs, (void*)&log};
+                  (void*)&sync, (void*)&max_sweeps, (void*)&tol, (void*)&tol_abs, (void*)&log, (void*)&ver};
   return coop_launch((const void*)jacobi_kernel, grid, NT, args, 0, ctx->stream);
 }
 
@@ -337,12 +470,14 @@ cudaError_t svd_post(qtt_ctx* ctx, const double* norms, Dim cnt, Dim len, Dim jl
 int* jacobi_log_slot(qtt_ctx* ctx) {
   Prof& p = ctx->prof;
   if (!p.d_log || p.log_used >= p.log_cap) return nullptr;
-  return p.d_log + 2 * (p.log_used++);
+  return p.d_log + 3 * (p.log_used++);
 }
 
 cudaError_t linalg_init(int device) {
-  cudaError_t e = cudaFuncSetAttribute((const void*)qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute((const void*)qr_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)qr_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -350,7 +485,7 @@ cudaError_t linalg_init(int device) {
 int coop_max_blocks(int num_sms) {
   int a = 0, b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)jacobi_kernel, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)qr_kernel, NT, 200 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)qr_kernel<double>, NT, 200 * 1024);
   int per = std::min(std::max(a, 1), std::max(b, 1));
   (void)per;
   // one CTA per SM: the FP64 pipe is per SM, more CTAs only add barrier traffic

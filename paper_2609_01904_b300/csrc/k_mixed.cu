@@ -1,0 +1,308 @@
+// Mixed-precision SVD of a small square bond factor (the reduced-precision
+// form of the step).
+//
+// Stage 1, FP32: one-sided Jacobi on the nv column vectors, all of them held
+// in the shared memory of one thread-block cluster (columns split across the
+// CTAs, partners reached through distributed shared memory), one hardware
+// cluster barrier per round of the circle schedule.  It stops at 1e-4
+// relative orthogonality, an order of magnitude above FP32 rounding.
+//
+// Stage 2, FP64 (host-driven GEMMs over the whole GPU, qtt_api.cu): Newton-
+// Schulz re-orthonormalisation J <- J (3I - J^T J)/2, W = R J, G = W^T W, a
+// simultaneous first-order Jacobi correction J <- J (I + Omega) with
+// Omega_ij = G_ij / (G_jj - G_ii), three times, then sigma_i = |W e_i| in FP64.
+// Singular values and right vectors come out accurate to FP64 rounding of R.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "k_mps.cuh"
+#include "qtt_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace qtt {
+
+namespace {
+
+constexpr int NT32 = 512;
+
+__device__ __forceinline__ void circle_pair32(int rd, int q, int P, int& i, int& j) {
+  const int R = P - 1;
+  if (q == 0) {
+    i = R;
+    j = rd;
+  } else {
+    i = (rd + q) % R;
+    j = (rd - q + R) % R;
+  }
+}
+
+// One warp per pair.  Columns are zero-padded to multiples of 128 floats (a
+// rotation keeps the padding zero), so a lane moves whole float4s: EA float4 of
+// each vector and EJ of each rotation column per lane.  Column c lives in the
+// shared memory of CTA c / cpc; its (distributed) address is looked up in a
+// table built once, so a round is one batch of vector loads, three warp
+// reductions, one batch of stores and one cluster barrier.
+template <int EA, int EJ>
+__global__ void __launch_bounds__(NT32) jacobi32_cluster_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
+                                                                Dim m_d, double* __restrict__ Jout, long long ldj,
+                                                                int cpc, int max_sweeps, float tol, float tol_abs,
+                                                                int* log) {
+  constexpr int MST = 128 * EA, JST = 128 * EJ;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks();
+  extern __shared__ float4 sm4[];
+  float* A = reinterpret_cast<float*>(sm4);   // cpc columns of MST floats
+  float* Jl = A + (long long)cpc * MST;       // cpc columns of JST floats
+  float4** pa = reinterpret_cast<float4**>(Jl + (long long)cpc * JST);  // per-column addresses
+  float4** pj = pa + (long long)cpc * CS;
+  __shared__ int s_cnt;
+  const int nv = (int)dv(nv_d), m = (int)dv(m_d);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT32 >> 5;
+
+  for (int cl_i = 0; cl_i < cpc; ++cl_i) {
+    const int c = rank * cpc + cl_i;
+    for (int l = tid; l < MST; l += NT32) A[cl_i * MST + l] = (c < nv && l < m) ? (float)V[c * ldv + l] : 0.f;
+    for (int l = tid; l < JST; l += NT32) Jl[cl_i * JST + l] = (c < nv && l == c) ? 1.f : 0.f;
+  }
+  for (int c = tid; c < cpc * CS; c += NT32) {
+    pa[c] = reinterpret_cast<float4*>(cl.map_shared_rank(A + (c % cpc) * MST, c / cpc));
+    pj[c] = reinterpret_cast<float4*>(cl.map_shared_rank(Jl + (c % cpc) * JST, c / cpc));
+  }
+  const int P = nv + (nv & 1), R = P - 1;
+  int sweep = 0;
+  for (sweep = 0; sweep < max_sweeps && nv >= 2; ++sweep) {
+    if (tid == 0) s_cnt = 0;
+    cl.sync();
+    for (int rd = 0; rd < R; ++rd) {
+      for (int q = rank + CS * warp; q < P / 2; q += CS * nw) {
+        int i, j;
+        if (q == 0) {
+          i = R;
+          j = rd;
+        } else {
+          i = rd + q;
+          if (i >= R) i -= R;
+          j = rd - q;
+          if (j < 0) j += R;
+        }
+        if (i >= nv || j >= nv) continue;
+        float4* xi = pa[i];
+        float4* xj = pa[j];
+        float4* ji = pj[i];
+        float4* jj = pj[j];
+        float4 x[EA], y[EA], u[EJ], w[EJ];
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+          x[e] = xi[lane + 32 * e];
+          y[e] = xj[lane + 32 * e];
+        }
+#pragma unroll
+        for (int e = 0; e < EJ; ++e) {
+          u[e] = ji[lane + 32 * e];
+          w[e] = jj[lane + 32 * e];
+        }
+        float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+          a = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, fmaf(x[e].z, x[e].z, fmaf(x[e].w, x[e].w, a))));
+          b = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, fmaf(y[e].z, y[e].z, fmaf(y[e].w, y[e].w, b))));
+          g = fmaf(x[e].x, y[e].x, fmaf(x[e].y, y[e].y, fmaf(x[e].z, y[e].z, fmaf(x[e].w, y[e].w, g))));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (g != 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b) && fabsf(g) > tol_abs * fmaxf(a, b)) {
+          const float zeta = (b - a) / (2.f * g);
+          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+#pragma unroll
+          for (int e = 0; e < EA; ++e) {
+            const float4 p = x[e], r = y[e];
+            xi[lane + 32 * e] = make_float4(cs * p.x - sn * r.x, cs * p.y - sn * r.y, cs * p.z - sn * r.z,
+                                            cs * p.w - sn * r.w);
+            xj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
+                                            sn * p.w + cs * r.w);
+          }
+#pragma unroll
+          for (int e = 0; e < EJ; ++e) {
+            const float4 p = u[e], r = w[e];
+            ji[lane + 32 * e] = make_float4(cs * p.x - sn * r.x, cs * p.y - sn * r.y, cs * p.z - sn * r.z,
+                                            cs * p.w - sn * r.w);
+            jj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
+                                            sn * p.w + cs * r.w);
+          }
+          if (lane == 0) atomicAdd(&s_cnt, 1);
+        }
+      }
+      cl.sync();
+    }
+    // rotations of this sweep over the cluster
+    int total = 0;
+    for (int r = 0; r < CS; ++r) total += *cl.map_shared_rank(&s_cnt, r);
+    cl.sync();  // every CTA has read the counters before the next sweep resets them
+    if (total == 0) break;
+  }
+  if (log && rank == 0 && tid == 0) {
+    log[0] = nv;
+    log[1] = m;
+    log[2] = sweep + 1;
+  }
+  for (int cl_i = 0; cl_i < cpc; ++cl_i) {
+    const int c = rank * cpc + cl_i;
+    if (c >= nv) continue;
+    for (int l = tid; l < nv; l += NT32) Jout[(long long)c * ldj + l] = (double)Jl[cl_i * JST + l];
+  }
+}
+
+// H = 1.5 I - 0.5 G  (the Newton-Schulz factor)
+__global__ void ns_factor_kernel(const double* G, double* H, long long ld, Dim n_d) {
+  const long long n = dv(n_d);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    H[i * ld + j] = -0.5 * G[i * ld + j] + (i == j ? 1.5 : 0.0);
+  }
+}
+
+// M = I + Omega^T with Omega_ij = G_ij / (G_jj - G_ii), the first-order angle
+// that zeroes G_ij; pairs whose angle is not small (nearly equal values) are
+// left alone
+__global__ void omega_kernel(const double* G, double* M, long long ld, Dim n_d) {
+  const long long n = dv(n_d);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    double v = 0.0;
+    if (i == j) {
+      v = 1.0;
+    } else {
+      // M[i][j] = Omega[j][i] = G_ji / (G_ii - G_jj)
+      const double gij = G[j * ld + i], den = G[i * ld + i] - G[j * ld + j];
+      if (den != 0.0) {
+        const double th = gij / den;
+        if (fabs(th) <= 0.1) v = th;
+      }
+    }
+    M[i * ld + j] = v;
+  }
+}
+
+// norms[c] = |W[c]| over m entries (rows of W, ld ldw)
+__global__ void row_norms_kernel(const double* W, long long ldw, Dim n_d, Dim m_d, double* norms) {
+  const long long n = dv(n_d), m = dv(m_d);
+  __shared__ double red[32];
+  for (long long c = blockIdx.x; c < n; c += gridDim.x) {
+    double s = 0.0;
+    for (long long l = threadIdx.x; l < m; l += blockDim.x) {
+      const double x = W[c * ldw + l];
+      s = fma(x, x, s);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) norms[c] = sqrt(s);
+  }
+}
+
+inline int eg(long long total) {
+  long long g = (total + 255) / 256;
+  return (int)std::max(1LL, std::min(g, 148LL * 8));
+}
+
+}  // namespace
+
+// FP32 cluster Jacobi: J (nv x nv, vector-major, ld ldj) from nv FP64 vectors
+// V (length m, ld ldv).  Sizes nvmax, mmax pick the cluster and smem layout.
+template <int EA, int EJ>
+static cudaError_t launch_j32(cudaLaunchConfig_t* cfg, const double* V, long long ldv, Dim nv, Dim m, double* J,
+                              long long ldj, int cpc, int* log) {
+  // FP32 stops an order of magnitude above its rounding floor; the FP64
+  // refinement squares the remaining non-orthogonality three times
+  const int max_sweeps = 20;
+  const float tol = 1e-4f, tol_abs = 1e-6f;
+  return cudaLaunchKernelEx(cfg, jacobi32_cluster_kernel<EA, EJ>, V, ldv, nv, m, J, ldj, cpc, max_sweeps, tol, tol_abs,
+                            log);
+}
+
+template <int EA, int EJ>
+static size_t j32_smem(int cpc, int CS) {
+  return (size_t)cpc * 128 * (EA + EJ) * sizeof(float) + 2 * (size_t)cpc * CS * sizeof(void*);
+}
+
+// FP32 cluster Jacobi: J (nv x nv, vector-major, ld ldj) from nv FP64 vectors
+// V (length m, ld ldv).  Sizes nvmax, mmax pick the cluster and smem layout:
+// about one pair per warp per round (16 warps per CTA), at most 16 CTAs.
+cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim nv, Dim m, long long nvmax,
+                             long long mmax, double* J, long long ldj) {
+  const int EA = (int)((mmax + 127) / 128), EJ = (int)((nvmax + 127) / 128);
+  if (EA > 4 || EJ > 4) return cudaErrorInvalidValue;
+  int CS = 1;
+  while (CS < 16 && (nvmax + 1) / 2 > (long long)CS * (NT32 / 32)) CS *= 2;
+  const long long budget = 200 * 1024;
+  while (CS < 16 && (long long)((nvmax + CS - 1) / CS) * 128 * (EA + EJ) * 4 > budget) CS *= 2;
+  const int cpc = (int)((nvmax + CS - 1) / CS);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(NT32);
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int* log = jacobi_log_slot(ctx);
+  const int key = EA * 10 + EJ;
+#define J32_CASE(a, b)                                          \
+  case a * 10 + b:                                              \
+    cfg.dynamicSmemBytes = j32_smem<a, b>(cpc, CS);              \
+    if (cfg.dynamicSmemBytes > (size_t)budget) return cudaErrorInvalidValue; \
+    return launch_j32<a, b>(&cfg, V, ldv, nv, m, J, ldj, cpc, log);
+  switch (key) {
+    J32_CASE(1, 1) J32_CASE(2, 2) J32_CASE(3, 3) J32_CASE(4, 4)
+    J32_CASE(1, 2) J32_CASE(2, 1) J32_CASE(2, 3) J32_CASE(3, 2) J32_CASE(3, 4) J32_CASE(4, 3)
+    J32_CASE(1, 3) J32_CASE(1, 4) J32_CASE(2, 4) J32_CASE(3, 1) J32_CASE(4, 1) J32_CASE(4, 2)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef J32_CASE
+}
+
+cudaError_t ns_factor(const double* G, double* H, long long ld, Dim n, long long nmax, cudaStream_t st) {
+  ns_factor_kernel<<<eg(nmax * nmax), 256, 0, st>>>(G, H, ld, n);
+  return cudaGetLastError();
+}
+
+cudaError_t omega_factor(const double* G, double* M, long long ld, Dim n, long long nmax, cudaStream_t st) {
+  omega_kernel<<<eg(nmax * nmax), 256, 0, st>>>(G, M, ld, n);
+  return cudaGetLastError();
+}
+
+cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st) {
+  row_norms_kernel<<<(int)std::max(1LL, std::min(nmax, 148LL * 4)), 256, 0, st>>>(W, ldw, n, m, norms);
+  return cudaGetLastError();
+}
+
+template <int EA, int EJ>
+static cudaError_t init_j32() {
+  const void* k = (const void*)jacobi32_cluster_kernel<EA, EJ>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+cudaError_t mixed_init() {
+  cudaError_t (*fs[])() = {init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
+                           init_j32<2, 1>, init_j32<2, 3>, init_j32<3, 2>, init_j32<3, 4>, init_j32<4, 3>,
+                           init_j32<1, 3>, init_j32<1, 4>, init_j32<2, 4>, init_j32<3, 1>, init_j32<4, 1>,
+                           init_j32<4, 2>};
+  for (auto f : fs) {
+    cudaError_t e = f();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace qtt

@@ -58,4 +58,12 @@ cudaError_t scale_rows(double* M, long long ldm, Dim ncols, const int* r_p, cons
 cudaError_t linalg_init(int device);
 int coop_max_blocks(int num_sms);
 
+// k_mixed.cu
+cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim nv, Dim m, long long nvmax,
+                             long long mmax, double* J, long long ldj);
+cudaError_t ns_factor(const double* G, double* H, long long ld, Dim n, long long nmax, cudaStream_t st);
+cudaError_t omega_factor(const double* G, double* M, long long ld, Dim n, long long nmax, cudaStream_t st);
+cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st);
+cudaError_t mixed_init();
+
 }  // namespace qtt

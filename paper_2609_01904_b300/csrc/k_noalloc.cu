@@ -34,7 +34,8 @@ constexpr long long kSq = kMaxRank * kMaxRank;
 constexpr long long kOffTq = 0, kOffTt = kOffTq + kBig, kOffQt = kOffTt + kBig, kOffTv = kOffQt + kBig,
                     kOffW1 = kOffTv + kBig, kOffRv = kOffW1 + kBig, kOffJv = kOffRv + kSq, kOffJh = kOffJv + kSq,
                     kOffJp = kOffJh + kSq, kOffNorm = kOffJp + kSq, kOffSig = kOffNorm + kMaxDim,
-                    kOffTau = kOffSig + kMaxDim, kOffInts = kOffTau + kMaxDim, kOffSync = kOffInts + 64,
+                    kOffTau = kOffSig + kMaxDim, kOffInts = kOffTau + kMaxDim, kOffFlags = kOffInts + 64,
+                    kOffSync = kOffFlags + (kMaxDim + 64) / 2,
                     kScratchDoubles = kOffSync + (long long)(sizeof(DevSync) / sizeof(double)) + 8;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -113,6 +114,7 @@ extern "C" qtt_status qtt_svd_trunc_noalloc(const double* M, int m, int n, doubl
   c.ws.d_sig = base + kOffSig;
   c.ws.d_tau = base + kOffTau;
   c.ws.d_ints = (int*)(base + kOffInts);
+  c.ws.d_flags = (int*)(base + kOffFlags);
   c.ws.d_sync = (DevSync*)(base + kOffSync);
   Workspace& s = c.ws;
   qtt_ctx* ctx = &c;

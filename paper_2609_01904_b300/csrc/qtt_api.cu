@@ -147,7 +147,8 @@ Caps step_caps(const qtt_ctx* ctx, const std::vector<int>& w, const std::vector<
 void ws_free(qtt_ctx* ctx) {
   Workspace& s = ctx->ws;
   double** bufs[] = {&s.d_carry, &s.d_x, &s.d_tv, &s.d_tq, &s.d_rv, &s.d_jv, &s.d_jp, &s.d_w1,
-                     &s.d_tt, &s.d_qt, &s.d_jh, &s.d_tau, &s.d_sig, &s.d_norm, &s.d_disc};
+                     &s.d_tt, &s.d_qt, &s.d_jh, &s.d_rg, &s.d_rh, &s.d_rt, &s.d_rw, &s.d_tau,
+                     &s.d_sig, &s.d_norm, &s.d_disc};
   for (double** b : bufs)
     if (*b) {
       cudaFree(*b);
@@ -155,6 +156,8 @@ void ws_free(qtt_ctx* ctx) {
     }
   if (s.d_ints) cudaFree(s.d_ints);
   s.d_ints = nullptr;
+  if (s.d_flags) cudaFree(s.d_flags);
+  s.d_flags = nullptr;
   if (s.d_sync) cudaFree(s.d_sync);
   s.d_sync = nullptr;
   Mps* ms[] = {s.phi, s.eta, s.theta, s.spare};
@@ -242,11 +245,16 @@ qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
   CK(cudaMalloc(&s.d_tt, tv * sizeof(double)));
   CK(cudaMalloc(&s.d_qt, tv * sizeof(double)));
   CK(cudaMalloc(&s.d_jh, s.jv * sizeof(double)));
+  CK(cudaMalloc(&s.d_rg, s.jv * sizeof(double)));
+  CK(cudaMalloc(&s.d_rh, s.jv * sizeof(double)));
+  CK(cudaMalloc(&s.d_rt, s.jv * sizeof(double)));
+  CK(cudaMalloc(&s.d_rw, s.jv * sizeof(double)));
   CK(cudaMalloc(&s.d_tau, s.vec * sizeof(double)));
   CK(cudaMalloc(&s.d_sig, s.vec * sizeof(double)));
   CK(cudaMalloc(&s.d_norm, s.vec * sizeof(double)));
   CK(cudaMalloc(&s.d_disc, 3 * (d + 1) * sizeof(double)));
   CK(cudaMalloc(&s.d_ints, 4 * (d + 8) * sizeof(int)));
+  CK(cudaMalloc(&s.d_flags, (s.vec + 64) * sizeof(int)));
   CK(cudaMalloc(&s.d_sync, sizeof(DevSync)));
   CK(cudaMemsetAsync(s.d_sync, 0, sizeof(DevSync), ctx->stream));
   CK(cudaMemsetAsync(s.d_disc, 0, 3 * (d + 1) * sizeof(double), ctx->stream));
@@ -317,6 +325,80 @@ GemmArgs gemm0();
 
 namespace {
 
+// contractions and QR in the step's precision; setup work is always FP64
+cudaError_t gemm_any(qtt_ctx* ctx, const GemmArgs& g, long long Mmax, long long Nmax, long long b1, long long b2) {
+  return ctx->use_mp ? gemm_f32(g, Mmax, Nmax, b1, b2, ctx->stream) : gemm_f64(g, Mmax, Nmax, b1, b2, ctx->stream);
+}
+
+cudaError_t qr_any(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
+                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
+  return ctx->use_mp ? qr_f32(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max)
+                     : qr_f64(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max);
+}
+
+// C (ld ldc) = A B with A (M x K, ld lda) and B (K x N, ld ldb), FP64
+GemmArgs mm(const double* A, long long lda, const double* B, long long ldb, double* C, long long ldc, Dim M, Dim K,
+            Dim N) {
+  GemmArgs g = gemm0();
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.sai = dconst(lda);
+  g.sak = dconst(1);
+  g.sbk = dconst(ldb);
+  g.sbj = dconst(1);
+  g.sci = dconst(ldc);
+  g.scj = dconst(1);
+  return g;
+}
+
+// G (ld ldg) = X X^T for X (rows x cols, ld ldx), FP64
+GemmArgs gram(const double* X, long long ldx, double* G, long long ldg, Dim rows, Dim cols) {
+  GemmArgs g = mm(X, ldx, X, ldx, G, ldg, rows, cols, rows);
+  g.sbk = dconst(1);
+  g.sbj = dconst(ldx);
+  return g;
+}
+
+// One-sided Jacobi of nv vectors V (length m) in the step's precision.  The
+// mixed form: FP32 Jacobi in one cluster, then FP64 refinement (Newton-Schulz
+// and three first-order corrections from the Gram of W = J V), sigma = |W_c|.
+qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, long long mmax,
+                      double* J, long long ldj, double* norms) {
+  if (!ctx->use_mp) {
+    KL(KC_JACOBI, jacobi_f64(ctx, V, ldv, nv, m, nvmax, J, ldj, norms));
+    return QTT_OK;
+  }
+  Workspace& s = ctx->ws;
+  const long long ld = ctx->ws_nvmax;
+  if (mmax > ld || nvmax > ld) return fail(QTT_EINVAL, "internal: mixed SVD wider than the workspace");
+  KL(KC_JACOBI, jacobi32_cluster(ctx, V, ldv, nv, m, nvmax, mmax, J, ldj));
+  auto ns = [&]() -> qtt_status {  // J <- (3I - J J^T)/2 J  (rows of J are the columns of the rotation)
+    KL(KC_REFINE, gemm_f64(gram(J, ldj, s.d_rg, ld, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, ns_factor(s.d_rg, s.d_rh, ld, nv, nvmax, ctx->stream));
+    KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
+                         ctx->stream));
+    return QTT_OK;
+  };
+  for (int it = 0; it < 3; ++it) {
+    CKS(ns());
+    KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_f64(gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, omega_factor(s.d_rg, s.d_rh, ld, nv, nvmax, ctx->stream));
+    KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
+                         ctx->stream));
+  }
+  CKS(ns());
+  KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
+  KL(KC_REFINE, row_norms(s.d_rw, ld, nv, m, nvmax, norms, ctx->stream));
+  return QTT_OK;
+}
+
 // Truncated SVD of nv vectors (rows of the vector-major array Tv, ld ell,
 // not modified).  J (nv x r) holds the kept right singular vectors of the
 // matrix M whose columns are the vectors: M J = U S.  Writes the kept rank
@@ -337,13 +419,13 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     Dim len = ell;
     if (ellmax > nvmax) {
       // M (ell x nv, column i = vector i) = Q R;  R column-major with ld ldv
-      KL(KC_QR, qr_f64(ctx, Tv, ell, s.d_tq, ellmax, ell, nv, nvmax, s.d_rv, false, nullptr, kq, ldv, 0));
-      KL(KC_JACOBI, jacobi_f64(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, s.d_jv, ldv, s.d_norm));
+      KL(KC_QR, qr_any(ctx, Tv, ell, s.d_tq, ellmax, ell, nv, nvmax, s.d_rv, false, nullptr, kq, ldv, 0));
+      CKS(jacobi_any(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, nvmax, s.d_jv, ldv, s.d_norm));
       len = dptr(kq);
     } else {
       KL(KC_COPY, copy2d(Tv, s.d_tq, nv, ell, ell, dconst(1), dconst(ellmax), dconst(1), nvmax * ellmax, 1.0,
-                ctx->stream));
-      KL(KC_JACOBI, jacobi_f64(ctx, s.d_tq, ellmax, nv, ell, nvmax, s.d_jv, ldv, s.d_norm));
+                         ctx->stream));
+      CKS(jacobi_any(ctx, s.d_tq, ellmax, nv, ell, nvmax, ellmax, s.d_jv, ldv, s.d_norm));
     }
     KL(KC_POST, svd_post(ctx, s.d_norm, nv, len, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt));
     return QTT_OK;
@@ -351,9 +433,10 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
   if (ellmax > ldv) return fail(QTT_EINVAL, "internal: SVD larger than the workspace");
   // M^T (nv x ell): its columns are the ell components, stored contiguously
   KL(KC_COPY, copy2d(Tv, s.d_tt, nv, ell, ell, dconst(1), dconst(1), dconst(nvmax), nvmax * ellmax, 1.0, ctx->stream));
-  KL(KC_QR, qr_f64(ctx, s.d_tt, dconst(nvmax), s.d_tq, nvmax, nv, ell, ellmax, s.d_rv, true, s.d_qt, kq, ellmax, nvmax));
+  KL(KC_QR, qr_any(ctx, s.d_tt, dconst(nvmax), s.d_tq, nvmax, nv, ell, ellmax, s.d_rv, true, s.d_qt, kq, ellmax,
+                   nvmax));
   // rows of R (kq x ell, ld ellmax) are the vectors of the reduced problem
-  KL(KC_JACOBI, jacobi_f64(ctx, s.d_rv, ellmax, dptr(kq), ell, ellmax, s.d_jh, ldv, s.d_norm));
+  CKS(jacobi_any(ctx, s.d_rv, ellmax, dptr(kq), ell, ellmax, ellmax, s.d_jh, ldv, s.d_norm));
   // J_v[c][i] = sum_j J_R[c][j] Q[i][j]
   GemmArgs g = gemm0();
   g.A = s.d_jh;
@@ -368,7 +451,7 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
   g.sbj = dptr(kq);
   g.sci = dconst(ldv);
   g.scj = dconst(1);
-  KL(KC_GEMM, gemm_f64(g, ellmax, nvmax, 1, 1, ctx->stream));
+  KL(KC_GEMM, gemm_any(ctx, g, ellmax, nvmax, 1, 1));
   KL(KC_POST, svd_post(ctx, s.d_norm, dptr(kq), ell, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt));
   return QTT_OK;
 }
@@ -411,7 +494,7 @@ qtt_status zipup_L(qtt_ctx* ctx, const Mpo* L, const Mps* psi, Mps* phi, const C
     g.sbj = dconst(1);
     g.sci = dptr(b2_p, 2);
     g.scj = dconst(1);
-    KL(KC_GEMM, gemm_f64(g, (long long)c.phi[k] * w, 2LL * c.psi[k + 1], 1, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, g, (long long)c.phi[k] * w, 2LL * c.psi[k + 1], 1, 1));
     const double* Wk = L->data + L->off[k];
     const long long tot = 2LL * c.phi[k] * w2 * c.psi[k + 1];
     if (k == d - 1) {  // w' = b' = 1: T is the last core
@@ -437,7 +520,7 @@ qtt_status zipup_L(qtt_ctx* ctx, const Mpo* L, const Mps* psi, Mps* phi, const C
     h.sbj = dconst(1);
     h.sci = ell;
     h.scj = dconst(1);
-    KL(KC_GEMM, gemm_f64(h, c.phi[k + 1], (long long)w2 * c.psi[k + 1], 1, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, h, c.phi[k + 1], (long long)w2 * c.psi[k + 1], 1, 1));
   }
   return QTT_OK;
 }
@@ -473,7 +556,7 @@ qtt_status zipup_C(qtt_ctx* ctx, const Mps* c2, const std::vector<int>& rc, cons
     g.sa1 = dptr(B2_p);
     g.sb1 = dconst(0);
     g.sc1 = dptr2(B_p, A2_p, R2);
-    KL(KC_GEMM, gemm_f64(g, c.phi[k], (long long)R2 * c.eta[k + 1], 2, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, g, c.phi[k], (long long)R2 * c.eta[k + 1], 2, 1));
     // T[(t,a')][(b,r)] = sum_r' B_k[r][t][r'] Z[t][b][r'][a']
     double* Tdst = (k == 0) ? eta->core(0) : s.d_tv;
     GemmArgs h = gemm0();
@@ -497,7 +580,7 @@ qtt_status zipup_C(qtt_ctx* ctx, const Mps* c2, const std::vector<int>& rc, cons
     h.sb2 = dptr(A2_p, R2);
     h.sc1 = dptr2(A2_p, B_p, R);
     h.sc2 = dconst(R);
-    KL(KC_GEMM, gemm_f64(h, R, c.eta[k + 1], 2, c.phi[k], ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, h, R, c.eta[k + 1], 2, c.phi[k]));
     if (k == 0) break;
     int* r_p = eta->ranks + k;
     const Dim nv = dptr(A2_p, 2), ell = dptr(B_p, R);
@@ -517,7 +600,7 @@ qtt_status zipup_C(qtt_ctx* ctx, const Mps* c2, const std::vector<int>& rc, cons
     q.sbj = nv;
     q.sci = dptr(r_p);
     q.scj = dconst(1);
-    KL(KC_GEMM, gemm_f64(q, (long long)c.phi[k] * R, c.eta[k], 1, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, q, (long long)c.phi[k] * R, c.eta[k], 1, 1));
   }
   return QTT_OK;
 }
@@ -577,7 +660,7 @@ qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
     int* kq_p = th->ranks + k + 1;  // becomes min(2 q_k, D_{k+1})
     const Dim m = dptr(q_p, 2), n = dptr(Dsave + k + 1);
     const long long ldw = 2LL * cap[k];
-    KL(KC_QR, qr_f64(ctx, s.d_tv, m, s.d_tq, ldw, m, n, cap[k + 1], s.d_rv, true, th->core(k), kq_p, cap[k + 1], ldw));
+    KL(KC_QR, qr_any(ctx, s.d_tv, m, s.d_tq, ldw, m, n, cap[k + 1], s.d_rv, true, th->core(k), kq_p, cap[k + 1], ldw));
     // next core (kq x 2 x D_{k+2}) = R (kq x D_{k+1}) theta_{k+1}
     GemmArgs g = gemm0();
     g.A = s.d_rv;
@@ -602,7 +685,7 @@ qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
       g.scj = dptr(kq_p);
       g.sc1 = dptr(kq_p);
     }
-    KL(KC_GEMM, gemm_f64(g, std::min<long long>(2LL * cap[k], cap[k + 1]), cap[k + 2], 2, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, g, std::min<long long>(2LL * cap[k], cap[k + 1]), cap[k + 2], 2, 1));
   }
   for (int k = d - 1; k >= 1; --k) {
     const int* q_p = th->ranks + k;  // rows of core k
@@ -627,7 +710,7 @@ qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
     g.sbj = dconst(1);
     g.sci = ell;
     g.scj = dconst(1);
-    KL(KC_GEMM, gemm_f64(g, out->cap[k], cap[k], 1, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, g, out->cap[k], cap[k], 1, 1));
     // core_{k-1} (q_{k-1} x 2 x r) = Q_{k-1} (q_{k-1} x 2 x q_k) W1^T
     const int* ql_p = th->ranks + k - 1;
     GemmArgs h = gemm0();
@@ -654,7 +737,7 @@ qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
       h.scj = dconst(1);
       h.sc1 = dptr(r_p);
     }
-    KL(KC_GEMM, gemm_f64(h, cap[k - 1], out->cap[k], 2, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, h, cap[k - 1], out->cap[k], 2, 1));
   }
   return QTT_OK;
 }
@@ -691,7 +774,7 @@ qtt_status tt_svd(qtt_ctx* ctx, const double* grid_dev, bool square, double eps,
     g.sbj = dconst(1);
     g.sci = dconst(ell);
     g.scj = dconst(1);
-    KL(KC_GEMM, gemm_f64(g, capk1, ell, 1, 1, ctx->stream));
+    KL(KC_GEMM, gemm_any(ctx, g, capk1, ell, 1, 1));
     std::swap(cur, nxt);
   }
   // last core (r_{d-1} x 2 x 1) is the remainder
@@ -718,7 +801,8 @@ qtt_status qtt_ctx_create(const qtt_params* p, void* stream, qtt_ctx** out) {
   if (p->n < 1 || p->n > 14) return fail(QTT_EINVAL, "n must be in 1..14");
   if (p->order != QTT_ORDER_SEQUENTIAL && p->order != QTT_ORDER_INTERLEAVED) return fail(QTT_EINVAL, "bad order");
   if (p->bc != QTT_BC_PERIODIC && p->bc != QTT_BC_ZERO) return fail(QTT_EINVAL, "bad boundary condition");
-  if (p->prec != QTT_FP64) return fail(QTT_EINVAL, "only the QTT_FP64 form is built in this library version");
+  if (p->prec != QTT_FP64 && p->prec != QTT_FP32)
+    return fail(QTT_EINVAL, "prec must be QTT_FP64 or QTT_FP32 (TF32/BF16 contractions are not built)");
   if (p->chi_max < 1 || p->chi_max > 1024) return fail(QTT_EINVAL, "chi_max must be in 1..1024");
   if (!(p->eps >= 0.0 && p->eps < 1.0)) return fail(QTT_EINVAL, "eps must be in [0, 1)");
   if (p->chi_zip < 0 || p->chi_zip > 1024 || p->chi_c < 0 || p->chi_c > 1024)
@@ -736,6 +820,7 @@ qtt_status qtt_ctx_create(const qtt_params* p, void* stream, qtt_ctx** out) {
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = linalg_init(c->device);
+  if (e == cudaSuccess) e = mixed_init();
   if (e != cudaSuccess) {
     delete c;
     return fail(QTT_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
@@ -942,6 +1027,11 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
   CKS(ensure_ws(ctx, L->w, rc));
   Caps c = step_caps(ctx, L->w, rc);
   Workspace& s = ctx->ws;
+  struct MpScope {  // the reduced-precision form applies inside the step only
+    qtt_ctx* c;
+    explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec == QTT_FP32); }
+    ~MpScope() { c->use_mp = false; }
+  } mp_scope(ctx);
   CKS(zipup_L(ctx, L, cur, s.phi, c));
   CKS(zipup_C(ctx, c2, rc, s.phi, s.eta, c));
   CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta));
@@ -1090,7 +1180,7 @@ qtt_status qtt_profile_start(qtt_ctx* ctx, int timing, int log_svd) {
   if (log_svd) {
     if (!p.d_log) {
       p.log_cap = 65536;
-      CK(cudaMalloc(&p.d_log, 2 * p.log_cap * sizeof(int)));
+      CK(cudaMalloc(&p.d_log, 3 * p.log_cap * sizeof(int)));
     }
   } else if (p.d_log) {
     cudaFree(p.d_log);
@@ -1112,16 +1202,19 @@ qtt_status qtt_profile_read(qtt_ctx* ctx, qtt_profile* out) {
     out->ms[p.cls[i]] += ms;
   }
   if (p.d_log && p.log_used > 0) {
-    std::vector<int> h(2 * p.log_used);
+    std::vector<int> h(3 * p.log_used);
     CK(cudaMemcpy(h.data(), p.d_log, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
     double f = 0.0;
+    long sweeps = 0;
     for (int i = 0; i < p.log_used; ++i) {
-      double a = h[2 * i], b = h[2 * i + 1];
+      double a = h[3 * i], b = h[3 * i + 1];
       double n = std::min(a, b), m = std::max(a, b);
       f += 6.0 * m * n * n + 20.0 * n * n * n;
+      sweeps += h[3 * i + 2];
     }
     out->svd_logged = p.log_used;
     out->svd_flops = f;
+    out->svd_sweeps = sweeps;
   }
   return device_status(ctx);
 }

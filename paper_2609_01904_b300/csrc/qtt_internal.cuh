@@ -48,10 +48,13 @@ __device__ __forceinline__ long long dv(const Dim& d) {
 struct DevSync {
   unsigned int bar_count;
   unsigned int bar_gen;
-  int counters[4];
+  int counters[4];   // rotations per sweep (4 rotating slots)
   int status;
-  int pad[9];
+  int done[4];       // CTAs that finished a sweep (same slots)
+  int pad[5];
 };
+
+
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
@@ -63,6 +66,28 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __device__ __forceinline__ void set_status(DevSync* s, int code) {
   atomicCAS(&s->status, 0, code);
+}
+
+// bounded waits on a counter written by another CTA of the same launch
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  return cuda::atomic_ref<const int, cuda::thread_scope_device>(*p).load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  cuda::atomic_ref<int, cuda::thread_scope_device>(*p).store(v, cuda::memory_order_release);
+}
+// thread 0 waits until *p >= target; false (status set) on timeout or error
+__device__ __forceinline__ bool wait_geq(const int* p, int target, DevSync* s) {
+  if (ld_acquire(p) >= target) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (ld_acquire(p) < target) {
+    if (ld_acquire(&s->status) != 0) return false;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      set_status(s, QTT_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(20);
+  }
+  return true;
 }
 
 // All CTAs of a cooperative launch call this the same number of times.
@@ -100,8 +125,9 @@ __device__ __forceinline__ bool grid_sync(DevSync* s) {
   return s_ok != 0;
 }
 
-// Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).
-__device__ __forceinline__ double block_sum(double v, double* red /* >= 32 */) {
+// Block-wide sum of one value per thread (blockDim.x a multiple of 32, <= 1024).
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red /* >= 32 */) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
@@ -109,12 +135,12 @@ __device__ __forceinline__ double block_sum(double v, double* red /* >= 32 */) {
   __syncthreads();
   int nw = blockDim.x >> 5;
   if (w == 0) {
-    double t = (l < nw) ? red[l] : 0.0;
+    T t = (l < nw) ? red[l] : T(0);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (l == 0) red[0] = t;
   }
   __syncthreads();
-  double r = red[0];
+  T r = red[0];
   __syncthreads();
   return r;
 }
@@ -163,6 +189,11 @@ struct Workspace {
   double* d_tt = nullptr;     // transposed vectors (wide SVDs)
   double* d_qt = nullptr;     // thin Q of a wide SVD
   double* d_jh = nullptr;     // Jacobi rotations of the reduced problem
+  int* d_flags = nullptr;     // per-column round counters / reflector flags
+  double* d_rg = nullptr;     // FP64 refinement of the mixed-precision SVD:
+  double* d_rh = nullptr;     //   Gram, Newton-Schulz / correction factor,
+  double* d_rt = nullptr;     //   product, rotated vectors (ws_nvmax^2 each)
+  double* d_rw = nullptr;
   double* d_tau = nullptr;    // Householder scalars
   double* d_sig = nullptr;    // singular values (sorted)
   double* d_norm = nullptr;   // vector norms from the Jacobi sweeps
@@ -178,7 +209,7 @@ struct Workspace {
 }  // namespace qtt
 
 namespace qtt {
-enum { KC_GEMM = 0, KC_QR, KC_JACOBI, KC_POST, KC_MPO, KC_SUM, KC_COPY, KC_FDTD, KC_OTHER, KC_N };
+enum { KC_GEMM = 0, KC_QR, KC_JACOBI, KC_POST, KC_MPO, KC_SUM, KC_COPY, KC_FDTD, KC_REFINE, KC_OTHER, KC_N };
 
 struct Prof {
   int timing = 0;
@@ -202,6 +233,7 @@ struct qtt_ctx {
   qtt::Workspace ws;
   bool ws_ready = false;
   qtt::Prof prof;
+  bool use_mp = false;      // inside a reduced-precision step: FP32 contractions and QR, mixed SVD
   long long ws_nvmax = 0;   // widest SVD (vectors) the workspace holds
   long long ws_ellmax = 0;  // longest vector of a step SVD
 };
@@ -224,6 +256,9 @@ struct GemmArgs {
 // C[b1,b2](i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j); Mmax/Nmax/nbmax size the grid.
 cudaError_t gemm_f64(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max,
                      long long nb2max, cudaStream_t st);
+// the same product with FP32 arithmetic (the reduced-precision form)
+cudaError_t gemm_f32(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max,
+                     long long nb2max, cudaStream_t st);
 
 // Householder QR of the m x n matrix whose column j is Ain + j*lda (length m).
 // R (kq x n, kq = min(m,n)) is written to Rout row-major (R[i][c] at i*ldr+c)
@@ -232,6 +267,11 @@ cudaError_t gemm_f64(const GemmArgs& a, long long Mmax, long long Nmax, long lon
 // ldr: leading dimension of a column-major R.  Q formation needs m <= qm_max
 // (the column is built in shared memory).
 cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n,
+                   long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
+                   long long qm_max = 0);
+// the same factorisation with FP32 arithmetic on an FP32 working copy (W is
+// reinterpreted as float storage); R and Q are written as doubles
+cudaError_t qr_f32(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n,
                    long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
                    long long qm_max = 0);
 

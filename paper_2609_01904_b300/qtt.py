@@ -47,13 +47,13 @@ _PI = ctypes.POINTER(ctypes.c_int)
 _PD = ctypes.POINTER(ctypes.c_double)
 _PL = ctypes.POINTER(ctypes.c_long)
 
-QTT_KCLASSES = 9
-KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "copy", "fdtd", "other"]
+QTT_KCLASSES = 10
+KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "copy", "fdtd", "refine", "other"]
 
 
 class qtt_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_long * QTT_KCLASSES), ("ms", ctypes.c_double * QTT_KCLASSES),
-                ("svd_logged", ctypes.c_long), ("svd_flops", ctypes.c_double)]
+                ("svd_logged", ctypes.c_long), ("svd_flops", ctypes.c_double), ("svd_sweeps", ctypes.c_long)]
 
 
 _SIGS = {
@@ -338,7 +338,7 @@ def qtt_profile_read(ctx: Ctx) -> dict:
     p = qtt_profile()
     _check(_lib.qtt_profile_read(ctx.h, ctypes.byref(p)), "qtt_profile_read")
     return {"launches": dict(zip(KERNEL_CLASSES, list(p.launches))), "ms": dict(zip(KERNEL_CLASSES, list(p.ms))),
-            "svd_logged": p.svd_logged, "svd_flops": p.svd_flops}
+            "svd_logged": p.svd_logged, "svd_flops": p.svd_flops, "svd_sweeps": p.svd_sweeps}
 
 
 __all__ = [n for n in EXPORTED] + ["Ctx", "Mps", "Mpo", "QttError", "qtt_params", "EXPORTED", "LIB_PATH"]

@@ -1,0 +1,107 @@
+"""The reduced-precision form (QTT_FP32: FP32 contractions and QR updates,
+truncation SVDs as FP32 Jacobi refined to FP64 accuracy) against the FP64
+oracle.
+
+Stated tolerance: one step from a shared state within 2e-5 + 1e-6 / g
+relative L2 of the oracle, g the smallest relative gap
+(sigma_r - sigma_{r+1}) / sigma_1 at any truncation cut of that step that
+discards a value (FP32 rounding of the contractions, ~1e-7 per product
+accumulated over the step's ~60 dependent factorisations, moves a truncated
+subspace by rounding / gap); ranks within 2 of the oracle's (a kept /
+discarded decision may flip for values within FP32 rounding of
+eps * sigma_1)."""
+import numpy as np
+import pytest
+
+from oracle import qtt_oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL_STEP = 2e-5
+
+
+def _tol(stats):
+    g = 1.0
+    for _kind, _k, S, r in stats:
+        if r < len(S) and S[0] > 0:
+            g = min(g, max((S[r - 1] - S[r]) / S[0], 1e-300))
+    return TOL_STEP + 1e-6 / g
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch  # noqa: F401
+    from paper_2609_01904_b300 import build
+    build.build()
+    from paper_2609_01904_b300 import qtt
+    return qtt
+
+
+def _t(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def _dense(q, psi, N):
+    import torch
+    out = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    q.qtt_to_dense(psi, out)
+    q.qtt_ctx_sync(psi.ctx)
+    return out.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("n,chi,order,bc", [(5, 16, "interleaved", "periodic"), (5, 16, "sequential", "zero"),
+                                            (8, 128, "interleaved", "periodic")])
+def test_fp32_form_one_step_from_random_state(q, n, chi, order, bc):
+    N = 1 << n
+    eps = 1e-7
+    c = W.layered_model(n, 40.0, 11) if n < 8 else W.constant_model(n, 2000.0)
+    lam2 = (0.5 / c.max()) ** 2
+    ctx = q.qtt_ctx_create(n=n, order=order, bc=bc, chi_max=chi, eps=eps, chi_c=12, eps_c=1e-8, prec="fp32")
+    prev_h = O.tt_round(W.random_tt_cores(2 * n, chi, 1, decay=0.05), 1e-14, chi)
+    cur_h = O.tt_round(W.random_tt_cores(2 * n, chi, 2, decay=0.05), 1e-14, chi)
+    L = q.qtt_laplacian_mpo(ctx)
+    C = q.qtt_velocity_mps(ctx, _t(c))
+    prev = q.qtt_mps_from_cores(ctx, prev_h)
+    cur = q.qtt_mps_from_cores(ctx, cur_h)
+    src = (N // 2 + 1, 3)
+    q.qtt_step(L, C, lam2, prev, cur, src, 0.37)
+    st = []
+    want = O.mps_step(O.laplacian_mpo(n, order, bc), O.velocity_mps(c, n, order, 1e-8, 12), lam2, prev_h, cur_h,
+                      eps, chi, src, 0.37, n, order, st)
+    got_r, want_r = q.qtt_mps_ranks(cur), O.mps_ranks(want)
+    assert max(abs(a - b) for a, b in zip(got_r, want_r)) <= 2, (got_r, want_r)
+    assert _rel(_dense(q, cur, N), O.mps_to_dense(want, n, order)) < _tol(st)
+
+
+def test_fp32_form_every_step_of_qtt64_run(q):
+    """All 300 steps of the 64x64 constant-velocity workload, teacher-forced
+    from the oracle's states, in the reduced-precision form."""
+    wl = W.config(0)
+    n, N = wl.n, wl.N
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    amps = wl.source_amplitudes(c)
+    ctx = q.qtt_ctx_create(n=n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                           eps_c=wl.eps_c, prec="fp32")
+    L = q.qtt_laplacian_mpo(ctx)
+    C = q.qtt_velocity_mps(ctx, _t(c))
+    Lo = O.laplacian_mpo(n, wl.order, wl.bc)
+    Co = O.velocity_mps(c, n, wl.order, wl.eps_c, wl.chi_c)
+    src = (N // 2 + 1, N // 2)
+    po, co = O.zero_mps(2 * n), O.zero_mps(2 * n)
+    worst, errs = 0.0, []
+    for k in range(wl.steps):
+        prev, cur = q.qtt_mps_from_cores(ctx, po), q.qtt_mps_from_cores(ctx, co)
+        q.qtt_step(L, C, lam2, prev, cur, src, float(amps[k]))
+        st = []
+        po, co = co, O.mps_step(Lo, Co, lam2, po, co, wl.eps, wl.chi, src, float(amps[k]), n, wl.order, st)
+        e = _rel(_dense(q, cur, N), O.mps_to_dense(co, n, wl.order))
+        errs.append(e)
+        worst = max(worst, e / _tol(st))
+    assert worst < 1.0, worst
+    assert np.median(errs) < TOL_STEP, np.median(errs)
