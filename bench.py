@@ -36,6 +36,7 @@ UNIT = "steps/s"
 WORKLOAD_IDX = 2
 MID_RUN = 2000
 FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 (148 SMs x 2032 MHz x ~4.2 FLOP/clk/SM)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 FMA pipes at the maximum SM clock
 
 
 def _peaks():
@@ -135,7 +136,7 @@ def run_ours(args, rank, world, local_rank):
     wl = W.config(WORKLOAD_IDX)
     c = wl.velocity()
     lam2 = wl.lambda2(c)
-    total = MID_RUN + args.warmup + args.steps + args.e2e_steps + 2
+    total = MID_RUN + max(args.warmup + args.steps + args.e2e_steps, args.err_steps) + 2
     amps = wl.source_amplitudes(c, total)
     stream = torch.cuda.Stream()
     ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
@@ -207,20 +208,26 @@ def run_ours(args, rank, world, local_rank):
     ms = prof["ms"]
     dom = max(ms, key=lambda kk: ms[kk])
     launches = prof["launches"]
-    if dom == "jacobi" and prof["svd_flops"] > 0 and ms["jacobi"] > 0:
-        achieved = prof["svd_flops"] / (ms["jacobi"] / 1e3) / 1e12
-        roof = {"kernel": "jacobi_kernel (one-sided Jacobi SVD, FP64)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 of the recipe (1.25 TFLOP/s); FP64 FMA probe measured 0.95",
-                "work": "6 m n^2 + 20 n^3 per SVD of the reduced n x m problem (Golub-Van Loan)",
-                "launches": launches["jacobi"], "avg_launch_ms": ms["jacobi"] / max(launches["jacobi"], 1),
-                "avg_sweeps": prof["svd_sweeps"] / max(prof["svd_logged"], 1)}
+    svd_flops = prof["svd_flops"]
+    roof = {"bound": "alu", "traffic": None, "launches": launches.get(dom, 0),
+            "avg_launch_ms": ms[dom] / max(launches.get(dom, 1), 1),
+            "avg_sweeps": prof["svd_sweeps"] / max(prof["svd_logged"], 1),
+            "work": "6 m n^2 + 20 n^3 per SVD of the reduced n x m factor (Golub-Van Loan), sizes logged per launch"}
+    if dom == "jacobi" and args.form == "fp64":
+        achieved = svd_flops / (ms["jacobi"] / 1e3) / 1e12
+        roof.update({"kernel": "jacobi_kernel (one-sided Jacobi SVD, FP64, cooperative)", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal FP64 of the recipe (1.25 TFLOP/s); FP64 FMA probe measured 0.95"})
+    elif dom == "jacobi":
+        achieved = svd_flops / (ms["jacobi"] / 1e3) / 1e12
+        roof.update({"kernel": "jacobi32_cluster_kernel (one-sided Jacobi SVD, FP32, one cluster)",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "FP32 FMA: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz; probe measured 63"})
     else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
+        roof.update({"kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None})
     roof["share_of_step"] = ms[dom] / max(sum(ms.values()), 1e-9)
-    roof["class_ms"] = {kk: round(v, 3) for kk, v in ms.items()}
+    roof["class_ms_per_step"] = {kk: round(v / args.steps, 3) for kk, v in ms.items() if v > 0}
 
     n_launch = int(sum(launches.values()))
     result = {
@@ -249,7 +256,70 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "step_ms": [round(x, 3) for x in step_ms],
     }
+    if args.compare and world == 1:
+        result["plain_fp64"], result["error"] = compare_forms(q, wl, c, amps, args)
+        if result["plain_fp64"]:
+            result["speedup_vs_plain_fp64"] = result["plain_fp64"]["ms_per_step"] / ms_per_step
     return result, (C, L, prev, cur, ctx)
+
+
+def compare_forms(q, wl, c, amps, args):
+    """The plain FP64 form timed on the same mid-run state, and the error of
+    both forms after args.err_steps steps: against each other, and against
+    the dense Eq. 2 update continued from the same dense field."""
+    import torch
+    N = wl.N
+    lam2 = wl.lambda2(c)
+    src = wl.sources[0]
+    rx = torch.as_tensor(np.array([r[0] for r in wl.receivers]), device="cuda")
+    rz = torch.as_tensor(np.array([r[1] for r in wl.receivers]), device="cuda")
+    out = {}
+    fields, traces = {}, {}
+    for form in ("fp64", args.form):
+        if form in fields:
+            continue
+        stream = torch.cuda.Stream()
+        ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                               eps_c=wl.eps_c, prec=form, stream=stream)
+        C, L, prev, cur = _setup_gpu_state(q, wl, ctx, c, amps, stream)
+        tr = torch.zeros((args.err_steps, len(wl.receivers)), dtype=torch.float64, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.err_steps + 1)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for kk in range(args.err_steps):
+                q.qtt_step(L, C, lam2, prev, cur, src, float(amps[MID_RUN + kk]))
+                ev[kk + 1].record(stream)
+                q.qtt_sample(cur, rx, rz, tr[kk])
+        q.qtt_ctx_sync(ctx)
+        if form == "fp64":
+            t = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.err_steps)]
+            out = {"ms_per_step": float(np.mean(t)), "value": 1000.0 / float(np.mean(t)), "unit": UNIT,
+                   "steps": args.err_steps, "note": "same state and steps as the error check, no L2 flush"}
+        dense = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        q.qtt_to_dense(cur, dense)
+        q.qtt_ctx_sync(ctx)
+        fields[form] = dense.cpu().numpy()
+        traces[form] = tr.cpu().numpy()
+        del prev, cur, C, L, ctx
+    # dense FDTD from the same dense state, same source samples
+    ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, prec="fp64")
+    c_dev = torch.as_tensor(c, device="cuda")
+    c2 = c_dev * c_dev
+    up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    uc, un = up.clone(), up.clone()
+    for kk in range(MID_RUN + args.err_steps):
+        q.qtt_fdtd_step(ctx, c2, lam2, up, uc, un, src, float(amps[kk]))
+        up, uc, un = uc, un, up
+    q.qtt_ctx_sync(ctx)
+    fd = uc.cpu().numpy()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    err = {"steps_from_mid_run": args.err_steps,
+           "field_rel_l2_vs_fp64_mps": rel(fields[args.form], fields["fp64"]),
+           "trace_rel_l2_vs_fp64_mps": rel(traces[args.form], traces["fp64"]),
+           "field_rel_l2_vs_dense_fdtd": {f: rel(fields[f], fd) for f in fields},
+           "threshold": 1e-3}
+    err["eligible"] = err["field_rel_l2_vs_fp64_mps"] <= 1e-3 and err["trace_rel_l2_vs_fp64_mps"] <= 1e-3
+    return out, err
 
 
 def oracle_baseline(seconds: float, mid_run: int = 600):
@@ -346,7 +416,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32"],
+                    help="fp32: the chosen form (FP32 contractions/QR, FP64-accurate SVDs); fp64: the plain form")
+    ap.add_argument("--compare", type=int, default=1, help="also time the plain FP64 form and measure errors")
+    ap.add_argument("--err-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

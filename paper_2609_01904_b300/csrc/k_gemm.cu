@@ -13,7 +13,7 @@ namespace qtt {
 
 namespace {
 
-constexpr int BM = 32, BN = 32, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
 struct GemmKArgs {
   GemmArgs a;

@@ -27,17 +27,6 @@ namespace {
 
 constexpr int NT32 = 512;
 
-__device__ __forceinline__ void circle_pair32(int rd, int q, int P, int& i, int& j) {
-  const int R = P - 1;
-  if (q == 0) {
-    i = R;
-    j = rd;
-  } else {
-    i = (rd + q) % R;
-    j = (rd - q + R) % R;
-  }
-}
-
 // One warp per pair.  Columns are zero-padded to multiples of 128 floats (a
 // rotation keeps the padding zero), so a lane moves whole float4s: EA float4 of
 // each vector and EJ of each rotation column per lane.  Column c lives in the
@@ -159,6 +148,163 @@ __global__ void __launch_bounds__(NT32) jacobi32_cluster_kernel(const double* __
   }
 }
 
+// Block one-sided Jacobi.  The nv columns form 2*CS blocks of B columns;
+// block k lives in the shared memory of CTA k/2 (slot k%2).  A sweep is a
+// round-robin tournament over the blocks: in each of its 2*CS-1 block rounds
+// CTA r copies its pair of blocks into a local working area, performs one
+// full local sweep over their 2B columns (2B-1 rounds of B disjoint pairs,
+// one warp per pair, separated by __syncthreads only), and writes the blocks
+// back.  One cluster barrier per block round instead of one per pair round.
+template <int EA, int EJ, int B>
+__global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
+                                                              Dim m_d, double* __restrict__ Jout, long long ldj,
+                                                              int max_sweeps, float tol, float tol_abs, int* log) {
+  constexpr int MST = 128 * EA, JST = 128 * EJ, W = 2 * B;
+  static_assert(B == NT32 / 32, "one warp per pair of a local round");
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks(), NB = 2 * CS;
+  extern __shared__ float4 sm4[];
+  float* hA = reinterpret_cast<float*>(sm4);  // home: 2 blocks x B columns
+  float* hJ = hA + 2 * B * MST;
+  float* wA = hJ + 2 * B * JST;               // working copy of the current block pair
+  float* wJ = wA + W * MST;
+  __shared__ int s_cnt;
+  const int nv = (int)dv(nv_d), m = (int)dv(m_d);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int k = 0; k < B; ++k) {
+      const int c = (2 * rank + s2) * B + k;
+      for (int l = tid; l < MST; l += NT32)
+        hA[(s2 * B + k) * MST + l] = (c < nv && l < m) ? (float)V[c * ldv + l] : 0.f;
+      for (int l = tid; l < JST; l += NT32) hJ[(s2 * B + k) * JST + l] = (c < nv && l == c) ? 1.f : 0.f;
+    }
+  int sweep = 0;
+  for (sweep = 0; sweep < max_sweeps && nv >= 2; ++sweep) {
+    if (tid == 0) s_cnt = 0;
+    cl.sync();
+    for (int t = 0; t < NB - 1; ++t) {
+      // this CTA's block pair in block round t (circle method over NB blocks)
+      int bp, bq;
+      if (rank == 0) {
+        bp = NB - 1;
+        bq = t;
+      } else {
+        bp = t + rank;
+        if (bp >= NB - 1) bp -= NB - 1;
+        bq = t - rank;
+        if (bq < 0) bq += NB - 1;
+      }
+      const int blk[2] = {bp, bq};
+      // copy in (float4 through distributed shared memory)
+      for (int h = 0; h < 2; ++h) {
+        const float4* srcA = reinterpret_cast<const float4*>(
+            cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
+        const float4* srcJ = reinterpret_cast<const float4*>(
+            cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
+        float4* dA = reinterpret_cast<float4*>(wA + h * B * MST);
+        float4* dJ = reinterpret_cast<float4*>(wJ + h * B * JST);
+        for (int e = tid; e < B * MST / 4; e += NT32) dA[e] = srcA[e];
+        for (int e = tid; e < B * JST / 4; e += NT32) dJ[e] = srcJ[e];
+      }
+      __syncthreads();
+      // full local sweep over the 2B columns
+      for (int lr = 0; lr < W - 1; ++lr) {
+        int i, j;
+        const int q = warp, R = W - 1;
+        if (q == 0) {
+          i = R;
+          j = lr;
+        } else {
+          i = lr + q;
+          if (i >= R) i -= R;
+          j = lr - q;
+          if (j < 0) j += R;
+        }
+        const int gi = blk[i / B] * B + (i % B), gj = blk[j / B] * B + (j % B);
+        if (gi < nv && gj < nv) {
+          float4* xi = reinterpret_cast<float4*>(wA + i * MST);
+          float4* xj = reinterpret_cast<float4*>(wA + j * MST);
+          float4* ui = reinterpret_cast<float4*>(wJ + i * JST);
+          float4* uj = reinterpret_cast<float4*>(wJ + j * JST);
+          float4 x[EA], y[EA], u[EJ], w[EJ];
+#pragma unroll
+          for (int e = 0; e < EA; ++e) {
+            x[e] = xi[lane + 32 * e];
+            y[e] = xj[lane + 32 * e];
+          }
+#pragma unroll
+          for (int e = 0; e < EJ; ++e) {
+            u[e] = ui[lane + 32 * e];
+            w[e] = uj[lane + 32 * e];
+          }
+          float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+          for (int e = 0; e < EA; ++e) {
+            a = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, fmaf(x[e].z, x[e].z, fmaf(x[e].w, x[e].w, a))));
+            b = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, fmaf(y[e].z, y[e].z, fmaf(y[e].w, y[e].w, b))));
+            g = fmaf(x[e].x, y[e].x, fmaf(x[e].y, y[e].y, fmaf(x[e].z, y[e].z, fmaf(x[e].w, y[e].w, g))));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+          }
+          if (g != 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b) && fabsf(g) > tol_abs * fmaxf(a, b)) {
+            const float zeta = (b - a) / (2.f * g);
+            const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            const float cs = rsqrtf(1.f + tt * tt), sn = cs * tt;
+#pragma unroll
+            for (int e = 0; e < EA; ++e) {
+              const float4 p = x[e], r = y[e];
+              xi[lane + 32 * e] = make_float4(cs * p.x - sn * r.x, cs * p.y - sn * r.y, cs * p.z - sn * r.z,
+                                              cs * p.w - sn * r.w);
+              xj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
+                                              sn * p.w + cs * r.w);
+            }
+#pragma unroll
+            for (int e = 0; e < EJ; ++e) {
+              const float4 p = u[e], r = w[e];
+              ui[lane + 32 * e] = make_float4(cs * p.x - sn * r.x, cs * p.y - sn * r.y, cs * p.z - sn * r.z,
+                                              cs * p.w - sn * r.w);
+              uj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
+                                              sn * p.w + cs * r.w);
+            }
+            if (lane == 0) atomicAdd(&s_cnt, 1);
+          }
+        }
+        __syncthreads();
+      }
+      // copy back to the home CTAs
+      for (int h = 0; h < 2; ++h) {
+        float4* dA = reinterpret_cast<float4*>(cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
+        float4* dJ = reinterpret_cast<float4*>(cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
+        const float4* sA = reinterpret_cast<const float4*>(wA + h * B * MST);
+        const float4* sJ = reinterpret_cast<const float4*>(wJ + h * B * JST);
+        for (int e = tid; e < B * MST / 4; e += NT32) dA[e] = sA[e];
+        for (int e = tid; e < B * JST / 4; e += NT32) dJ[e] = sJ[e];
+      }
+      cl.sync();
+    }
+    int total = 0;
+    for (int r = 0; r < CS; ++r) total += *cl.map_shared_rank(&s_cnt, r);
+    cl.sync();  // every CTA has read the counters before the next sweep resets them
+    if (total == 0) break;
+  }
+  if (log && rank == 0 && tid == 0) {
+    log[0] = nv;
+    log[1] = m;
+    log[2] = sweep + 1;
+  }
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int k = 0; k < B; ++k) {
+      const int c = (2 * rank + s2) * B + k;
+      if (c >= nv) continue;
+      for (int l = tid; l < nv; l += NT32) Jout[(long long)c * ldj + l] = (double)hJ[(s2 * B + k) * JST + l];
+    }
+}
+
 // H = 1.5 I - 0.5 G  (the Newton-Schulz factor)
 __global__ void ns_factor_kernel(const double* G, double* H, long long ld, Dim n_d) {
   const long long n = dv(n_d);
@@ -255,6 +401,25 @@ cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim n
   cfg.numAttrs = 1;
   int* log = jacobi_log_slot(ctx);
   const int key = EA * 10 + EJ;
+  // block kernel: 2*CS blocks of 16 columns, 4 blocks of shared memory per CTA
+  {
+    constexpr int Bk = NT32 / 32;
+    int CSb = 1;
+    while (CSb < 16 && 2LL * CSb * Bk < nvmax) CSb *= 2;
+    const size_t sm_b = (size_t)4 * Bk * 128 * (EA + EJ) * sizeof(float);
+    if (2LL * CSb * Bk >= nvmax && sm_b <= (size_t)budget && (EA == EJ) && EA <= 2) {
+      cfg.gridDim = dim3(CSb);
+      at[0].val.clusterDim.x = CSb;
+      cfg.dynamicSmemBytes = sm_b;
+      const int max_sweeps = 20;
+      const float tol = 1e-4f, tol_abs = 1e-6f;
+      if (EA == 1)
+        return cudaLaunchKernelEx(&cfg, jacobi32_block_kernel<1, 1, Bk>, V, ldv, nv, m, J, ldj, max_sweeps, tol,
+                                  tol_abs, log);
+      return cudaLaunchKernelEx(&cfg, jacobi32_block_kernel<2, 2, Bk>, V, ldv, nv, m, J, ldj, max_sweeps, tol, tol_abs,
+                                log);
+    }
+  }
 #define J32_CASE(a, b)                                          \
   case a * 10 + b:                                              \
     cfg.dynamicSmemBytes = j32_smem<a, b>(cpc, CS);              \
@@ -293,8 +458,16 @@ static cudaError_t init_j32() {
   return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+template <int EA, int EJ>
+static cudaError_t init_jb() {
+  const void* k = (const void*)jacobi32_block_kernel<EA, EJ, NT32 / 32>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 cudaError_t mixed_init() {
-  cudaError_t (*fs[])() = {init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
+  cudaError_t (*fs[])() = {init_jb<1, 1>, init_jb<2, 2>,init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
                            init_j32<2, 1>, init_j32<2, 3>, init_j32<3, 2>, init_j32<3, 4>, init_j32<4, 3>,
                            init_j32<1, 3>, init_j32<1, 4>, init_j32<2, 4>, init_j32<3, 1>, init_j32<4, 1>,
                            init_j32<4, 2>};
