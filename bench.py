@@ -263,6 +263,100 @@ def run_ours(args, rank, world, local_rank):
     return result, (C, L, prev, cur, ctx)
 
 
+SHOTS_IDX = 3
+SHOTS_MID_RUN = 1000
+
+
+def run_shots(args):
+    """The 64-shot workload (512x512 layered section, per-shot bond caps
+    drawn from {32, 64, 128, 256}, FP32 form): MPS shot-steps per second of
+    the batched step, and the same shots stepped one after another on one
+    stream for comparison.  Each shot starts from its own mid-run state (its
+    dense Eq. 2 field at step 1000, compressed by the library)."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+
+    wl = W.config(SHOTS_IDX)
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    chis = [int(x) for x in W.chi_per_shot(wl.seed, len(wl.sources))]
+    ns = len(chis)
+    total = SHOTS_MID_RUN + args.warmup + args.steps + 4
+    amps = wl.source_amplitudes(c, total)
+    stream = torch.cuda.Stream()
+    t0 = time.time()
+    batch = q.qtt_batch_create(wl.n, ns, chis, order=wl.order, bc=wl.bc, chi_max=max(chis), eps=wl.eps,
+                               chi_c=wl.chi_c, eps_c=wl.eps_c, prec=args.form, stream=stream)
+    N = wl.N
+    with torch.cuda.stream(stream):
+        c_dev = torch.as_tensor(c, device="cuda")
+        C = q.qtt_velocity_mps(batch.ctxs[0], c_dev)
+        L = q.qtt_laplacian_mpo(batch.ctxs[0])
+        c2 = c_dev * c_dev
+        prev, cur = [], []
+        for s in range(ns):
+            up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+            uc, un = up.clone(), up.clone()
+            for k in range(SHOTS_MID_RUN):
+                q.qtt_fdtd_step(batch.ctxs[s], c2, lam2, up, uc, un, wl.sources[s], float(amps[k]))
+                up, uc, un = uc, un, up
+            prev.append(q.qtt_mps_from_dense(batch.ctxs[s], up))
+            cur.append(q.qtt_mps_from_dense(batch.ctxs[s], uc))
+    stream.synchronize()
+    setup_s = time.time() - t0
+    k = SHOTS_MID_RUN
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            q.qtt_step_batched(batch, L, C, lam2, prev, cur, wl.sources, [float(amps[k])] * ns)
+            k += 1
+    stream.synchronize()
+    ranks0 = [max(q.qtt_mps_ranks(x)) for x in cur]
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for x in batch.ctxs:
+        q.qtt_profile_start(x, timing=False, log_svd=False)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                q.qtt_step_batched(batch, L, C, lam2, prev, cur, wl.sources, [float(amps[k])] * ns)
+                evs[i][1].record(stream)
+                k += 1
+        torch.cuda.synchronize()
+    launches = sum(sum(q.qtt_profile_read(x)["launches"].values()) for x in batch.ctxs)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_per_step = float(np.mean(step_ms))
+    value = ns * args.steps / (float(np.sum(step_ms)) / 1e3)
+    # the same shots, one after another on the batch's stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.fill_(-1.0)
+        e0.record(stream)
+        for s in range(ns):
+            q.qtt_step(L, C, lam2, prev[s], cur[s], wl.sources[s], float(amps[k]))
+        e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    return {
+        "metric": "MPS shot-steps/s, 64 shots on a 2^18 grid, per-shot chi in {32,64,128,256} (1 B300)",
+        "value": value, "unit": "shot-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.form == "fp64" else "f32+f64", "data": "synthetic (seeded layered section)",
+        "config": {"workload": wl.name, "n": wl.n, "shots": ns, "chi_per_shot": chis, "eps": wl.eps,
+                   "form": args.form, "state": f"mid-run (step {SHOTS_MID_RUN})", "max_rank_start": ranks0,
+                   "l2": "flushed between timed steps (256 MiB write)", "setup_s": round(setup_s, 1)},
+        "gpu_launches": int(launches),
+        "sequential": {"ms_per_batch_step": seq_ms, "value": ns / (seq_ms / 1e3),
+                       "note": "the same 64 shot-steps issued one after another on one stream"},
+        "speedup_vs_sequential": seq_ms / ms_per_step,
+        "clocks": clk.summary(),
+        "step_ms": [round(x, 3) for x in step_ms],
+    }
+
+
 def compare_forms(q, wl, c, amps, args):
     """The plain FP64 form timed on the same mid-run state, and the error of
     both forms after args.err_steps steps: against each other, and against
@@ -422,6 +516,8 @@ def main():
     ap.add_argument("--err-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="qtt1024_marmousi", choices=["qtt1024_marmousi", "qtt512_64shots"],
+                    help="qtt512_64shots: the batched multi-shot step instead of the headline workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -432,6 +528,10 @@ def main():
         res = run_reference(args, rank, world)
         if res is not None:
             print(json.dumps(res), flush=True)
+        return
+    if args.workload == "qtt512_64shots":
+        if rank == 0:
+            print(json.dumps(run_shots(args)), flush=True)
         return
     if world > 1:
         import torch

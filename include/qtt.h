@@ -155,6 +155,30 @@ qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, doubl
 qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2,
                     qtt_mps* psi_prev, qtt_mps* psi_cur, const long* src_ixiz, double src_amp);
 
+/* Batched shots.  A batch holds one context per shot (each with its own
+ * chi_max and workspace, all on `cuda_stream`) and a pool of min(nshots, 8)
+ * internal streams; qtt_step_batched advances every shot by one step
+ * (Eq. 17), shot i on pool stream i mod 8, so that shots of different pool
+ * streams run concurrently on the GPU; one host thread per pool stream
+ * issues the launches.  The cooperative grids of each shot are capped so
+ * that the pool's grids fit on the device together.  The batched step is
+ * ordered after earlier work on `cuda_stream`, and later work on it waits for
+ * every shot.  Shot i's states are created in qtt_batch_ctx(batch, i) (owned
+ * by the batch: never passed to qtt_ctx_destroy).  chi_per_shot: nshots host
+ * ints, 0 = base->chi_max; NULL = all base->chi_max.  qtt_batch_destroy
+ * frees the contexts: destroy the shots' states first. */
+typedef struct qtt_batch qtt_batch;
+qtt_status qtt_batch_create(const qtt_params* base, int nshots, const int* chi_per_shot, void* cuda_stream,
+                            qtt_batch** out);
+qtt_ctx* qtt_batch_ctx(qtt_batch* batch, int shot);
+/* L and c2 are shared by all shots (created in any context of the same n,
+ * order and boundary condition).  prev, cur: nshots handles each, created in
+ * the shots' contexts; they rotate as in qtt_step.  src_ixiz: NULL, or
+ * 2*nshots host longs {ix_0, iz_0, ix_1, ...}; src_amp: nshots doubles. */
+qtt_status qtt_step_batched(qtt_batch* batch, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps** prev,
+                            qtt_mps** cur, const long* src_ixiz, const double* src_amp);
+void qtt_batch_destroy(qtt_batch* batch);
+
 /* ---------------------------------------------------------------- readout */
 
 /* Receiver readout: out[p] = A_0[s_0] A_1[s_1] ... A_{d-1}[s_{d-1}] (Eq. 8)

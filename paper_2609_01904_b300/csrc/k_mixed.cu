@@ -10,8 +10,13 @@
 // Stage 2, FP64 (host-driven GEMMs over the whole GPU, qtt_api.cu): Newton-
 // Schulz re-orthonormalisation J <- J (3I - J^T J)/2, W = R J, G = W^T W, a
 // simultaneous first-order Jacobi correction J <- J (I + Omega) with
-// Omega_ij = G_ij / (G_jj - G_ii), three times, then sigma_i = |W e_i| in FP64.
-// Singular values and right vectors come out accurate to FP64 rounding of R.
+// Omega_ij = G_ij / (G_jj - G_ii) (damped inside clusters of near-equal
+// values), three times, then sigma_i = |W e_i| in FP64.  The rotation is
+// orthogonal to FP64 rounding; the contamination of every vector by the
+// directions of much larger values (FP32 rounding of the first stage) is
+// removed, so well separated values come out to FP64 accuracy, while values
+// within ~1e-7 sigma_1 of each other near the FP32 floor stay resolved only
+// to about 1e-7 sigma_1.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -314,23 +319,53 @@ __global__ void ns_factor_kernel(const double* G, double* H, long long ld, Dim n
   }
 }
 
-// M = I + Omega^T with Omega_ij = G_ij / (G_jj - G_ii), the first-order angle
-// that zeroes G_ij; pairs whose angle is not small (nearly equal values) are
-// left alone
-__global__ void omega_kernel(const double* G, double* M, long long ld, Dim n_d) {
+// Omega_ji = G_ij / (G_ii - G_jj): the first-order angle of the pair (i, j)
+// that zeroes G_ij (Omega is antisymmetric).  Pairs whose angle is not small
+// (nearly equal values) are left alone.
+__device__ __forceinline__ double omega_angle(const double* G, long long ld, long long i, long long j) {
+  const double gij = G[i * ld + j], den = G[i * ld + i] - G[j * ld + j];
+  if (den == 0.0) return 0.0;
+  const double th = gij / den;
+  return fabs(th) <= 0.1 ? th : 0.0;
+}
+
+// Angles above kSmallAngle only occur between nearly equal values (in
+// practice inside the noise floor of the spectrum); they are the ones damped.
+constexpr double kSmallAngle = 1e-3;
+
+// rs[i] = sum over j of |Omega_ji| (= |Omega_ij|) with |Omega_ji| > kSmallAngle, one block per row
+__global__ void omega_rowsum_kernel(const double* G, long long ld, Dim n_d, double* rs) {
+  const long long n = dv(n_d);
+  __shared__ double red[32];
+  for (long long i = blockIdx.x; i < n; i += gridDim.x) {
+    double a = 0.0;
+    for (long long j = threadIdx.x; j < n; j += blockDim.x)
+      if (j != i) {
+        const double th = fabs(omega_angle(G, ld, i, j));
+        if (th > kSmallAngle) a += th;
+      }
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) rs[i] = a;
+  }
+}
+
+// M = I + Omega'^T.  Angles up to kSmallAngle are kept as they are (with at
+// most 512 vectors their row sums stay below 0.52); larger ones are scaled by
+// min(1, 1/(4 max(rs_i, rs_j))), so their row sums stay below 1/4.  Omega' is
+// antisymmetric, so ||Omega'||_2 <= 0.77 and ||I + Omega'||_2 <= 1.26 <
+// sqrt(3): the Newton-Schulz iteration that follows always converges.  Without
+// the damping, clusters of near-equal tiny values can give ||I + Omega|| > 2
+// and the iteration diverges.
+__global__ void omega_kernel(const double* G, const double* rs, double* M, long long ld, Dim n_d) {
   const long long n = dv(n_d);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / n, j = e % n;
-    double v = 0.0;
-    if (i == j) {
-      v = 1.0;
-    } else {
-      // M[i][j] = Omega[j][i] = G_ji / (G_ii - G_jj)
-      const double gij = G[j * ld + i], den = G[i * ld + i] - G[j * ld + j];
-      if (den != 0.0) {
-        const double th = gij / den;
-        if (fabs(th) <= 0.1) v = th;
-      }
+    double v = 1.0;
+    if (i != j) {
+      // M[i][j] = Omega'_ji
+      v = omega_angle(G, ld, i, j);
+      const double r = fmax(rs[i], rs[j]);
+      if (fabs(v) > kSmallAngle && r > 0.25) v *= 0.25 / r;
     }
     M[i * ld + j] = v;
   }
@@ -440,8 +475,12 @@ cudaError_t ns_factor(const double* G, double* H, long long ld, Dim n, long long
   return cudaGetLastError();
 }
 
-cudaError_t omega_factor(const double* G, double* M, long long ld, Dim n, long long nmax, cudaStream_t st) {
-  omega_kernel<<<eg(nmax * nmax), 256, 0, st>>>(G, M, ld, n);
+cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, Dim n, long long nmax,
+                         cudaStream_t st) {
+  omega_rowsum_kernel<<<(int)std::max(1LL, std::min(nmax, 148LL * 4)), 256, 0, st>>>(G, ld, n, rs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  omega_kernel<<<eg(nmax * nmax), 256, 0, st>>>(G, rs, M, ld, n);
   return cudaGetLastError();
 }
 

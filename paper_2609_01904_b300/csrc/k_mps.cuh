@@ -62,7 +62,9 @@ int coop_max_blocks(int num_sms);
 cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim nv, Dim m, long long nvmax,
                              long long mmax, double* J, long long ldj);
 cudaError_t ns_factor(const double* G, double* H, long long ld, Dim n, long long nmax, cudaStream_t st);
-cudaError_t omega_factor(const double* G, double* M, long long ld, Dim n, long long nmax, cudaStream_t st);
+// rs: nmax doubles of scratch (row sums of |Omega|)
+cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, Dim n, long long nmax,
+                         cudaStream_t st);
 cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st);
 cudaError_t mixed_init();
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -365,7 +366,8 @@ GemmArgs gram(const double* X, long long ldx, double* G, long long ldg, Dim rows
 
 // One-sided Jacobi of nv vectors V (length m) in the step's precision.  The
 // mixed form: FP32 Jacobi in one cluster, then FP64 refinement (Newton-Schulz
-// and three first-order corrections from the Gram of W = J V), sigma = |W_c|.
+// and three damped first-order corrections from the Gram of W = J V, two
+// final Newton-Schulz steps), sigma = |W_c|.
 qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, long long mmax,
                       double* J, long long ldj, double* norms) {
   if (!ctx->use_mp) {
@@ -388,11 +390,12 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
     CKS(ns());
     KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
     KL(KC_REFINE, gemm_f64(gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
-    KL(KC_REFINE, omega_factor(s.d_rg, s.d_rh, ld, nv, nvmax, ctx->stream));
+    KL(KC_REFINE, omega_factor(s.d_rg, norms, s.d_rh, ld, nv, nvmax, ctx->stream));  // norms: scratch here
     KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
     KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
                          ctx->stream));
   }
+  CKS(ns());
   CKS(ns());
   KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
   KL(KC_REFINE, row_norms(s.d_rw, ld, nv, m, nvmax, norms, ctx->stream));
@@ -1039,6 +1042,112 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
   // prev now holds u^{k+1}: exchange buffers so that prev = u^k, cur = u^{k+1}
   std::swap(prev->data, cur->data);
   std::swap(prev->ranks, cur->ranks);
+  return QTT_OK;
+}
+
+}  // extern "C"
+
+struct qtt_batch {
+  std::vector<qtt_ctx*> ctx;
+  std::vector<cudaStream_t> pool;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t start = nullptr;
+  cudaStream_t user = nullptr;
+};
+
+extern "C" {
+
+void qtt_batch_destroy(qtt_batch* b) {
+  if (!b) return;
+  for (cudaStream_t st : b->pool) cudaStreamSynchronize(st);
+  for (qtt_ctx* c : b->ctx) qtt_ctx_destroy(c);
+  for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+  if (b->start) cudaEventDestroy(b->start);
+  for (cudaStream_t st : b->pool) cudaStreamDestroy(st);
+  delete b;
+}
+
+qtt_status qtt_batch_create(const qtt_params* base, int nshots, const int* chi_per_shot, void* stream,
+                            qtt_batch** out) {
+  if (!base || !out || nshots < 1) return fail(QTT_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  qtt_batch* b = new qtt_batch();
+  b->user = (cudaStream_t)stream;
+  const int S = std::min(nshots, 8);
+  for (int i = 0; i < S; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      qtt_batch_destroy(b);
+      return fail(QTT_ECUDA, "stream pool");
+    }
+    b->pool.push_back(st);
+    b->done.push_back(ev);
+  }
+  if (cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) != cudaSuccess) {
+    qtt_batch_destroy(b);
+    return fail(QTT_ECUDA, "event");
+  }
+  for (int i = 0; i < nshots; ++i) {
+    qtt_params p = *base;
+    if (chi_per_shot && chi_per_shot[i] > 0) p.chi_max = chi_per_shot[i];
+    qtt_ctx* c = nullptr;
+    qtt_status st = qtt_ctx_create(&p, b->user, &c);
+    if (st != QTT_OK) {
+      qtt_batch_destroy(b);
+      return st;
+    }
+    // the pool's cooperative grids must be co-resident together
+    c->coop_blocks = std::max(8, c->num_sms / S);
+    b->ctx.push_back(c);
+  }
+  *out = b;
+  return QTT_OK;
+}
+
+qtt_ctx* qtt_batch_ctx(qtt_batch* b, int shot) {
+  if (!b || shot < 0 || shot >= (int)b->ctx.size()) return nullptr;
+  return b->ctx[shot];
+}
+
+qtt_status qtt_step_batched(qtt_batch* b, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps** prev,
+                            qtt_mps** cur, const long* src, const double* amp) {
+  if (!b || !L || !c2 || !prev || !cur) return fail(QTT_EINVAL, "null argument");
+  if (src && !amp) return fail(QTT_EINVAL, "source positions without amplitudes");
+  const int n = (int)b->ctx.size(), S = (int)b->pool.size();
+  for (int i = 0; i < n; ++i)
+    if (!prev[i] || !cur[i] || prev[i]->ctx != b->ctx[i] || cur[i]->ctx != b->ctx[i])
+      return fail(QTT_EINVAL, "state " + std::to_string(i) + " does not belong to its shot's context");
+  CK(cudaEventRecord(b->start, b->user));
+  for (int s = 0; s < S; ++s) CK(cudaStreamWaitEvent(b->pool[s], b->start, 0));
+  // each shot's step runs on its pool stream; every other call on a shot's
+  // context stays on the batch's stream
+  for (int i = 0; i < n; ++i) b->ctx[i]->stream = b->pool[i % S];
+  std::vector<qtt_status> st(S, QTT_OK);
+  std::vector<std::string> msg(S);
+  auto worker = [&](int s) {
+    for (int i = s; i < n; i += S) {
+      qtt_status r = qtt_step(b->ctx[i], L, c2, lambda2, prev[i], cur[i], src ? src + 2 * i : nullptr,
+                              src ? amp[i] : 0.0);
+      if (r != QTT_OK) {
+        st[s] = r;
+        msg[s] = g_err;
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int s = 1; s < S; ++s) th.emplace_back(worker, s);
+  worker(0);
+  for (auto& t : th) t.join();
+  for (int i = 0; i < n; ++i) b->ctx[i]->stream = b->user;
+  for (int s = 0; s < S; ++s) {
+    CK(cudaEventRecord(b->done[s], b->pool[s]));
+    CK(cudaStreamWaitEvent(b->user, b->done[s], 0));
+  }
+  for (int s = 0; s < S; ++s)
+    if (st[s] != QTT_OK) return fail(st[s], "shot on pool stream " + std::to_string(s) + ": " + msg[s]);
   return QTT_OK;
 }
 

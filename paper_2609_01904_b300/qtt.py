@@ -76,20 +76,25 @@ _SIGS = {
     "qtt_fdtd_step": [_P, _P, _D, _P, _P, _P, _L, _L, _D],
     "qtt_last_step_discarded": [_P, _PD],
     "qtt_profile_start": [_P, _I, _I],
+    "qtt_batch_create": [ctypes.POINTER(qtt_params), _I, _PI, _P, ctypes.POINTER(_P)],
+    "qtt_step_batched": [_P, _P, _P, _D, ctypes.POINTER(_P), ctypes.POINTER(_P), _PL, _PD],
     "qtt_profile_read": [_P, ctypes.POINTER(qtt_profile)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
-for _name in ("qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy"):
+for _name in ("qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_batch_destroy"):
     getattr(_lib, _name).argtypes = [_P]
     getattr(_lib, _name).restype = None
+_lib.qtt_batch_ctx.argtypes = [_P, _I]
+_lib.qtt_batch_ctx.restype = _P
 _lib.qtt_last_error.argtypes = []
 _lib.qtt_last_error.restype = ctypes.c_char_p
 
 # every symbol include/qtt.h declares
-EXPORTED = sorted(list(_SIGS) + ["qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_last_error"])
+EXPORTED = sorted(list(_SIGS) + ["qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_last_error",
+                                  "qtt_batch_destroy", "qtt_batch_ctx"])
 
 
 def _check(st: int, where: str) -> None:
@@ -106,9 +111,10 @@ def _dev_ptr(t, dtype_name: str = "float64") -> int:
 
 
 class Ctx:
-    def __init__(self, handle: int, params: qtt_params):
+    def __init__(self, handle: int, params: qtt_params, owner=None):
         self.h = handle
         self.params = params
+        self.owner = owner  # a batch owns its shots' contexts; states keep it alive
 
     @property
     def n(self) -> int:
@@ -119,9 +125,9 @@ class Ctx:
         return 2 * self.params.n
 
     def __del__(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "owner", None) is None:
             _lib.qtt_ctx_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 class Mps:
@@ -328,6 +334,74 @@ def qtt_last_step_discarded(ctx: Ctx):
     out = np.zeros(3 * (ctx.d - 1))
     _check(_lib.qtt_last_step_discarded(ctx.h, out.ctypes.data_as(_PD)), "qtt_last_step_discarded")
     return out.reshape(3, ctx.d - 1)
+
+
+class _BatchHandle:
+    def __init__(self, handle: int):
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qtt_batch_destroy(self.h)
+            self.h = None
+
+
+class Batch:
+    """Handle of a qtt_batch; .ctxs[i] is shot i's context.  The C batch is
+    destroyed once the Batch, its contexts and their states are all gone."""
+
+    def __init__(self, hold: _BatchHandle, ctxs: list):
+        self.hold = hold
+        self.ctxs = ctxs
+
+    @property
+    def h(self) -> int:
+        return self.hold.h
+
+
+def qtt_batch_create(n: int, nshots: int, chi_per_shot=None, order: str = "interleaved", bc: str = "periodic",
+                     chi_max: int = 32, eps: float = 1e-10, chi_c: int = 0, eps_c: float = 0.0, prec: str = "fp64",
+                     stream=None) -> Batch:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, 0, 0.0, chi_c, eps_c, 0)
+    chis = None
+    if chi_per_shot is not None:
+        chis = (ctypes.c_int * nshots)(*[int(x) for x in chi_per_shot])
+    h = _P()
+    _check(_lib.qtt_batch_create(ctypes.byref(p), nshots, chis, _P(stream.cuda_stream), ctypes.byref(h)),
+           "qtt_batch_create")
+    hold = _BatchHandle(h.value)
+    ctxs = []
+    for i in range(nshots):
+        chi_i = int(chi_per_shot[i]) if chi_per_shot is not None and int(chi_per_shot[i]) > 0 else chi_max
+        pi = qtt_params(p.n, p.order, p.bc, p.prec, chi_i, eps, 0, 0.0, chi_c, eps_c, 0)
+        ctxs.append(Ctx(_lib.qtt_batch_ctx(hold.h, i), pi, owner=hold))
+    return Batch(hold, ctxs)
+
+
+def qtt_batch_ctx(batch: Batch, shot: int) -> Ctx:
+    return batch.ctxs[shot]
+
+
+def qtt_batch_destroy(batch: Batch) -> None:
+    """Drops the Python references; the C batch goes with the last state."""
+    batch.ctxs = []
+    batch.hold = None
+
+
+def qtt_step_batched(batch: Batch, L: Mpo, c2: Mps, lambda2: float, prev: list, cur: list, src=None,
+                     amp=None) -> None:
+    n = len(batch.ctxs)
+    P = (_P * n)(*[x.h for x in prev])
+    C = (_P * n)(*[x.h for x in cur])
+    s = a = None
+    if src is not None:
+        s = (ctypes.c_long * (2 * n))(*[int(v) for xy in src for v in xy])
+        a = (ctypes.c_double * n)(*[float(v) for v in amp])
+    _check(_lib.qtt_step_batched(batch.h, L.h, c2.h, lambda2, P, C, s, a), "qtt_step_batched")
+    # the library exchanged each pair's buffers; the handles keep their roles
 
 
 def qtt_profile_start(ctx: Ctx, timing: bool = False, log_svd: bool = False) -> None:

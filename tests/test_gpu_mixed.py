@@ -105,3 +105,78 @@ def test_fp32_form_every_step_of_qtt64_run(q):
         worst = max(worst, e / _tol(st))
     assert worst < 1.0, worst
     assert np.median(errs) < TOL_STEP, np.median(errs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_chi256_step_on_the_512_grid(q, prec):
+    """The widest bond cap of the multi-shot workload (n = 9, chi = 256, cap
+    binding at the middle bonds): Jacobi SVDs of up to 512 vectors."""
+    n, chi, eps = 9, 256, 1e-7
+    N = 1 << n
+    c = W.layered_model(n, 6.25, 4)
+    lam2 = (0.5 / c.max()) ** 2
+    ctx = q.qtt_ctx_create(n=n, chi_max=chi, eps=eps, chi_c=12, eps_c=1e-8, prec=prec)
+    prev_h = O.tt_round(W.random_tt_cores(2 * n, chi, 1, decay=0.01), 1e-14, chi)
+    cur_h = O.tt_round(W.random_tt_cores(2 * n, chi, 2, decay=0.01), 1e-14, chi)
+    assert max(O.mps_ranks(cur_h)) == chi
+    L = q.qtt_laplacian_mpo(ctx)
+    C = q.qtt_velocity_mps(ctx, _t(c))
+    prev = q.qtt_mps_from_cores(ctx, prev_h)
+    cur = q.qtt_mps_from_cores(ctx, cur_h)
+    src = (N // 2 + 1, 3)
+    q.qtt_step(L, C, lam2, prev, cur, src, 0.37)
+    st = []
+    want = O.mps_step(O.laplacian_mpo(n, "interleaved", "periodic"), O.velocity_mps(c, n, "interleaved", 1e-8, 12),
+                      lam2, prev_h, cur_h, eps, chi, src, 0.37, n, "interleaved", st)
+    got_r, want_r = q.qtt_mps_ranks(cur), O.mps_ranks(want)
+    err = _rel(_dense(q, cur, N), O.mps_to_dense(want, n, "interleaved"))
+    if prec == "fp64":
+        assert got_r == want_r
+        assert err < 1e-10, err
+    else:
+        assert max(abs(a - b) for a, b in zip(got_r, want_r)) <= 2, (got_r, want_r)
+        assert err < _tol(st), (err, _tol(st))
+
+
+def test_fp32_form_steps_from_a_mid_run_state_of_the_64_shot_workload(q):
+    """Shot 1 of the 64-shot workload (n = 9, chi = 256, layered section):
+    the oracle's own dense Eq. 2 run to step 1000 compressed by the oracle,
+    then five FP32-form steps teacher-forced against the oracle.  The steep
+    spectrum of such states has a wide cluster of near-equal tiny singular
+    values, where an undamped first-order refinement diverges.  The chi cap
+    falls on near-degenerate values here (relative gaps ~1e-8), where the
+    truncated subspace is not unique and the gap-based tolerance is void, so
+    each step is held to the workload's accuracy target, 1e-3 relative L2."""
+    wl = W.config(3)
+    n, N = wl.n, wl.N
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    chi = int(W.chi_per_shot(wl.seed, len(wl.sources))[1])
+    assert chi == 256
+    src = wl.sources[1]
+    mid = 1000
+    amps = wl.source_amplitudes(c, mid + 8)
+    up, uc = np.zeros((N, N)), np.zeros((N, N))
+    for k in range(mid):
+        up, uc = uc, O.fdtd_step(up, uc, c * c, lam2, wl.bc, src, float(amps[k]))
+    po = O.state_from_dense(up, n, wl.order, wl.eps, chi)
+    co = O.state_from_dense(uc, n, wl.order, wl.eps, chi)
+    Lo = O.laplacian_mpo(n, wl.order, wl.bc)
+    Co = O.velocity_mps(c, n, wl.order, wl.eps_c, wl.chi_c)
+    ctx = q.qtt_ctx_create(n=n, order=wl.order, bc=wl.bc, chi_max=chi, eps=wl.eps, chi_c=wl.chi_c, eps_c=wl.eps_c,
+                           prec="fp32")
+    L = q.qtt_laplacian_mpo(ctx)
+    C = q.qtt_velocity_mps(ctx, _t(c))
+    for k in range(mid, mid + 5):
+        prev, cur = q.qtt_mps_from_cores(ctx, po), q.qtt_mps_from_cores(ctx, co)
+        q.qtt_step(L, C, lam2, prev, cur, src, float(amps[k]))
+        st = []
+        want = O.mps_step(Lo, Co, lam2, po, co, wl.eps, chi, src, float(amps[k]), n, wl.order, st)
+        got_r, want_r = q.qtt_mps_ranks(cur), O.mps_ranks(want)
+        # eps = 1e-7 sits at FP32 resolution: every value within ~1e-7 sigma_1
+        # of the threshold may fall either side, so ranks agree more loosely
+        assert max(got_r) <= chi
+        assert max(abs(a - b) for a, b in zip(got_r, want_r)) <= 8, (k, got_r, want_r)
+        err = _rel(_dense(q, cur, N), O.mps_to_dense(want, n, wl.order))
+        assert err < min(_tol(st), 1e-3), (k, err, _tol(st))
+        po, co = co, want
