@@ -245,3 +245,24 @@ def chi_per_shot(seed: int = 4, shots: int = 64) -> np.ndarray:
     """Per-shot bond caps drawn uniformly from {32, 64, 128, 256}."""
     rng = np.random.default_rng(seed)
     return rng.choice(np.array([32, 64, 128, 256]), size=shots)
+
+
+def mlp_params(seed: int = 7, n_feat: int = 40, width: int = 128) -> np.ndarray:
+    """Initial parameters of the rank-proposal MLP, flat float32 in the layout
+    W1 (width x n_feat), b1, W2 (width x width), b2, W3 (1 x width), b3:
+    weights uniform in +-sqrt(6 / fan_in) (He et al. 2015), biases zero,
+    except b3 = 0.5 (the middle of the scaled-rank range)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for rows, cols in ((width, n_feat), (width, width), (1, width)):
+        lim = np.sqrt(6.0 / cols)
+        parts.append(rng.uniform(-lim, lim, size=(rows, cols)).ravel())
+        parts.append(np.zeros(rows))
+    parts[-1][:] = 0.5
+    return np.concatenate(parts).astype(np.float32)
+
+
+def gaussian_sketch(seed: int = 11, rows: int = 1024, cols: int = 512) -> np.ndarray:
+    """Fixed Gaussian test matrix (standard normal, float64, row-major) for the
+    randomised range finder; bond k uses its top-left block."""
+    return np.random.default_rng(seed).standard_normal((rows, cols))
