@@ -67,7 +67,7 @@ typedef enum { QTT_FP64 = 0, QTT_TF32 = 1, QTT_BF16 = 2, QTT_FP32 = 3 } qtt_prec
  * truncation of the state (Sec. 4.3).  chi_zip, eps_zip: truncation inside
  * the two zip-up applications (0 = use chi_max / eps).  chi_c, eps_c:
  * truncation of the c^2 MPS (the paper does not say; 0 = chi_max / 1e-8).
- * use_learned_rank: reserved, must be 0. */
+ * use_learned_rank: 1 enables the learned rounding (qtt_set_rank_model). */
 typedef struct {
   int n;
   int order;
@@ -178,6 +178,71 @@ qtt_ctx* qtt_batch_ctx(qtt_batch* batch, int shot);
 qtt_status qtt_step_batched(qtt_batch* batch, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps** prev,
                             qtt_mps** cur, const long* src_ixiz, const double* src_amp);
 void qtt_batch_destroy(qtt_batch* batch);
+
+/* ------------------------------------------------------------ learned form
+ * The rounding rule of Sec. 4.3 stays the judge; a learned model only
+ * proposes, per bond, the rank of the next step's round, whose SVD then first
+ * tries a randomised range finder of width proposal + oversample (Halko,
+ * Martinsson & Tropp 2011, Algorithm 4.1 with the direct SVD of Sec. 5.1):
+ * Y = X^T Omega, Y = QR, B = Q^T X^T, SVD of B, for X the bond matrix
+ * (q_k x 2 r_{k+1}) and Omega the top-left block of a caller-provided
+ * Gaussian matrix.  An exact check in FP64 accepts the sketch only if the rule
+ * is met: with rho = ||X - X Q Q^T||_F and c = #{sigma_i(B) >= eps sigma_1(B)},
+ * c < chi needs rho <= eps sigma_1(B); c >= chi needs
+ * rho^2 <= ((1 + 0.05)^2 - 1) sum_{i>=chi} sigma_i(B)^2, which keeps the
+ * discarded weight within (1.05)^2 of the optimum (Ky Fan's maximum
+ * principle on X X^T = A A^T + E E^T, A = X Q Q^T, E = X - A); c >= width
+ * rejects.
+ * A rejected bond takes the full SVD.  Each attempt costs one host
+ * synchronisation (the flag decides which kernels follow).
+ *
+ * The model: an MLP of 3 linear layers (40 -> 128 -> 128 -> 1, ReLU, FP32)
+ * reading 40 features of a bond's spectrum at step k (qtt_rank_features) and
+ * returning the bond's rank at step k+1 divided by chi_max; proposal =
+ * clamp(ceil(chi_max * y), 1, chi_max).  Parameters are one flat float array
+ * of qtt_mlp_param_count() values: W1 (128 x 40, row-major), b1 (128),
+ * W2 (128 x 128), b2 (128), W3 (1 x 128), b3 (1).  Training: mean squared
+ * error, Adam (Kingma & Ba 2015, Algorithm 1), on `cuda_stream` of the
+ * network. */
+typedef struct qtt_mlp qtt_mlp;
+int qtt_mlp_param_count(void);
+/* params: host, qtt_mlp_param_count() floats (copied).  max_batch: the most
+ * samples one forward or gradient call takes (>= 2n to serve a context). */
+qtt_status qtt_mlp_create(const float* params, int max_batch, void* cuda_stream, qtt_mlp** out);
+void qtt_mlp_destroy(qtt_mlp* mlp);
+/* X: device, n x 40 row-major floats; y: device, n floats. */
+qtt_status qtt_mlp_forward(qtt_mlp* mlp, const float* X, int n, float* y);
+/* Mean squared error against t (device, n floats) into *loss (device float,
+ * may be NULL) and its gradient, kept for qtt_mlp_adam_step and copied to
+ * grad (device, qtt_mlp_param_count() floats) when grad is not NULL. */
+qtt_status qtt_mlp_grad(qtt_mlp* mlp, const float* X, const float* t, int n, float* loss, float* grad);
+/* One Adam update from the last gradient (step count kept by the network). */
+qtt_status qtt_mlp_adam_step(qtt_mlp* mlp, float lr, float beta1, float beta2, float eps);
+qtt_status qtt_mlp_get_params(qtt_mlp* mlp, float* params);
+/* Features of bonds 1..nb (row k-1 of X, 40 floats each) from descending
+ * singular values S (device; row k at S + k*lds holds len[k] values) and the
+ * kept ranks ranks[k] (device ints), for rule parameters eps, chi and d sites:
+ * 0..31 log10(S_p/S_0) at p = floor(j (len-1)/31), clipped to [-16, 0], / 16;
+ * 32 rank/chi; 33 log10(discarded weight / S_0^2) clipped to [-32, 0], / 32;
+ * 34 log10(eps)/16; 35 k/d; 36 min(2^k, 2^(d-k), chi)/chi;
+ * 37 #{S_i >= eps S_0}/chi; 38 len/(2 chi); 39 1 (-1 for undefined logs). */
+qtt_status qtt_rank_features(const double* S, int lds, const int* len, const int* ranks, int nb, double eps, int chi,
+                             int d, float* X, void* cuda_stream);
+/* Features of bonds 1..d-1 of the last step's round (its logged spectra and
+ * the ranks of psi, the state that step produced), on the context stream. */
+qtt_status qtt_step_features(qtt_ctx* ctx, const qtt_mps* psi, float* X);
+/* Learned rounding for a context created with use_learned_rank = 1: sketch
+ * (device, rows x cols row-major doubles, not copied, kept alive by the
+ * caller) and oversample p; mlp (may be NULL) proposes the ranks after every
+ * step.  sketch = NULL turns the learned rounding off. */
+qtt_status qtt_set_rank_model(qtt_ctx* ctx, qtt_mlp* mlp, const double* sketch, int rows, int cols, int oversample);
+/* Proposals (host, d+1 ints; 0 = none) for the next step only, instead of
+ * the model's. */
+qtt_status qtt_set_proposals(qtt_ctx* ctx, const int* prop);
+/* The proposals the model made after the last step (host, d+1 ints). */
+qtt_status qtt_get_proposals(qtt_ctx* ctx, int* prop);
+/* Range-finder attempts and accepted attempts since the context was made. */
+qtt_status qtt_learned_stats(qtt_ctx* ctx, long* attempts, long* accepts);
 
 /* ---------------------------------------------------------------- readout */
 

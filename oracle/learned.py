@@ -11,11 +11,11 @@ keeps that rule as the judge and only changes how the kept subspace is found:
   features of a bond's singular-value spectrum at step k and proposes the
   bond's rank at step k+1 (the proposal is chi * output, rounded up);
 * the round's SVD of that bond at step k+1 then uses a randomised range
-  finder of width r_hat + p (Halko, Martinsson & Tropp, SIAM Review 2011,
+  finder of width r_hat + p (p = 16) (Halko, Martinsson & Tropp, SIAM Review 2011,
   Algorithm 4.1 followed by the direct SVD of Sec. 5.1): Y = X^T Omega,
   Q = qr(Y), B = Q^T X^T, SVD of B;
 * an exact check decides whether the sketch is good enough for the Sec. 4.3
-  rule; if not, the bond falls back to the full SVD.
+  rule (``range_finder_svd``); if not, the bond falls back to the full SVD.
 
 Training: mean squared error on the scaled rank, Adam (Kingma & Ba, ICLR 2015,
 Algorithm 1).  Parameters and the Gaussian test matrix come from the seeded
@@ -32,7 +32,7 @@ from oracle import qtt_oracle as O
 N_FEAT = 40
 WIDTH = 128
 N_SPEC = 32  # spectrum samples among the features
-OVERSAMPLE = 8
+OVERSAMPLE = 16
 TAU = 0.05
 
 # flat parameter layout: W1 (WIDTH x N_FEAT), b1, W2 (WIDTH x WIDTH), b2, W3 (1 x WIDTH), b3
@@ -163,12 +163,20 @@ def range_finder_svd(X: np.ndarray, Omega: np.ndarray, eps: float, chi: int, tau
     Acceptance, with c = #{Sb_i >= eps Sb_0}:
       c >= ks: reject (the cut is not inside the sketch);
       c <  chi (uncapped): accept iff rho <= eps Sb_0; every discarded
-               direction then has a singular value <= eps Sb_0 <= eps sigma_1;
+               direction then has a singular value <= sqrt(2) eps sigma_1
+               (Weyl on X X^T = A A^T + E E^T below: sigma_{r+1}(X)^2 <=
+               Sb_{r+1}^2 + rho^2);
       c >= chi (capped at chi): accept iff
-               ||X||^2 - sum_{i<chi} Sb_i^2
-                   <= (1+tau)^2 max(0, ||X||^2 - sum_{i<chi} (Sb_i + rho)^2),
-               the right side a lower bound of the optimal tail (Weyl:
-               sigma_i(X) <= Sb_i + rho).
+               rho^2 <= ((1+tau)^2 - 1) sum_{i>=chi} Sb_i^2.
+               Why: X X^T = A A^T + E E^T with A = X Q Q^T and E = X - A
+               (A E^T = 0), so by Ky Fan's maximum principle
+               sum_{i<chi} sigma_i(X)^2 <= sum_{i<chi} Sb_i^2 + ||E||_F^2 and
+               the optimal tail ||X||^2 - sum_{i<chi} sigma_i(X)^2 is at
+               least sum_{i>=chi} Sb_i^2; the sketch's discarded weight is
+               sum_{i>=chi} Sb_i^2 + rho^2, hence within (1+tau)^2 of the
+               optimum.  (Bounding each sigma_i(X) <= Sb_i + rho instead, by
+               Weyl, leaves a cross term 2 rho sum Sb_i that exceeds the tail
+               on every realistic bond, so that form never accepts.)
     Returns (accepted, r, Vt (r x m), US (l x r), Sb, rho)."""
     X = np.asarray(X, dtype=np.float64)
     Y = X.T @ Omega
@@ -181,7 +189,6 @@ def range_finder_svd(X: np.ndarray, Omega: np.ndarray, eps: float, chi: int, tau
     s0 = Sb[0] if len(Sb) else 0.0
     c = int(np.count_nonzero(Sb >= eps * s0)) if s0 > 0 else 0
     r = O.trunc_rank(Sb, eps, chi)
-    nx2 = float(np.sum(X * X))
     if s0 == 0.0:
         accepted = rho == 0.0
     elif c >= ks:
@@ -189,9 +196,7 @@ def range_finder_svd(X: np.ndarray, Omega: np.ndarray, eps: float, chi: int, tau
     elif c < chi:
         accepted = rho <= eps * s0
     else:
-        disc = nx2 - float(np.sum(Sb[:chi] ** 2))
-        lower = max(0.0, nx2 - float(np.sum((Sb[:chi] + rho) ** 2)))
-        accepted = disc <= (1.0 + tau) ** 2 * lower
+        accepted = rho * rho <= ((1.0 + tau) ** 2 - 1.0) * float(np.sum(Sb[chi:] ** 2))
     Vt = (Q @ Ub[:, :r]).T
     US = Vbt[:r].T * Sb[:r]
     return accepted, r, Vt, US, Sb, rho
@@ -240,14 +245,14 @@ def tt_round_learned(A: list[np.ndarray], eps: float, chi: int, proposals, G: np
 
 
 def mps_step_learned(L, c2, lambda2, prev, cur, eps, chi, src, amp, n, order, proposals, G,
-                     stats=None, log=None):
+                     stats=None, log=None, p: int = OVERSAMPLE, tau: float = TAU):
     """Eq. 17 step whose round uses tt_round_learned."""
     phi = O.zipup_lr(L, cur, eps, chi, stats)
     eta = O.zipup_rl(O.diagonal_mpo(c2), phi, eps, chi, stats)
     terms = [(2.0, cur), (-1.0, prev), (lambda2, eta)]
     if src is not None:
         terms.append((amp, O.product_state(src[0], src[1], n, order)))
-    return tt_round_learned(O.mps_sum(terms), eps, chi, proposals, G, stats=stats, log=log)
+    return tt_round_learned(O.mps_sum(terms), eps, chi, proposals, G, p=p, tau=tau, stats=stats, log=log)
 
 
 def round_spectra(stats: list, d: int) -> dict:

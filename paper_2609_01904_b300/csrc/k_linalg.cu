@@ -343,7 +343,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* V, long long ldv, Di
 __global__ void __launch_bounds__(1024) svd_post_kernel(const double* norms, Dim cnt_d, Dim len_d, Dim jlen_d,
                                                         const double* J, long long ldj, double eps, int chi,
                                                         int rank_cap, int* rank_out, double* sigma_out,
-                                                        double* disc_out, double* Jp, double* Jt, DevSync* sync) {
+                                                        double* disc_out, double* Jp, double* Jt, DevSync* sync,
+                                                        int* nsv_out) {
   extern __shared__ double sh[];
   // cnt rotated vectors (norms), each a combination of jlen input vectors
   // (row perm_j of J has jlen entries); they span min(cnt, len) directions
@@ -392,6 +393,7 @@ __global__ void __launch_bounds__(1024) svd_post_kernel(const double* norms, Dim
     for (int i = r; i < nv; ++i) dsum += ss[i] * ss[i];
     s_r = r;
     if (rank_out) *rank_out = r;
+    if (nsv_out) *nsv_out = nsv;
     if (disc_out) *disc_out = dsum;
   }
   __syncthreads();
@@ -459,11 +461,11 @@ cudaError_t jacobi_f64(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lo
 
 cudaError_t svd_post(qtt_ctx* ctx, const double* norms, Dim cnt, Dim len, Dim jlen, const double* J, long long ldj,
                      double eps, int chi, int rank_cap, int* rank_out, double* sigma_out, double* disc_out,
-                     double* Jp, double* Jt) {
+                     double* Jp, double* Jt, int* nsv_out) {
   long long nvmax = ldj;
   size_t smem = (size_t)nvmax * (2 * sizeof(double) + sizeof(int)) + 16;
   svd_post_kernel<<<1, 1024, smem, ctx->stream>>>(norms, cnt, len, jlen, J, ldj, eps, chi, rank_cap, rank_out,
-                                                  sigma_out, disc_out, Jp, Jt, ctx->ws.d_sync);
+                                                  sigma_out, disc_out, Jp, Jt, ctx->ws.d_sync, nsv_out);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 #include <utility>
 #include <vector>
 
+#include "k_learned.cuh"
 #include "k_mps.cuh"
 #include "qtt_internal.cuh"
 
@@ -161,6 +162,15 @@ void ws_free(qtt_ctx* ctx) {
   s.d_flags = nullptr;
   if (s.d_sync) cudaFree(s.d_sync);
   s.d_sync = nullptr;
+  void** lbufs[] = {(void**)&s.d_spec, (void**)&s.d_spec_len, (void**)&s.d_prop, (void**)&s.d_feat, (void**)&s.d_y,
+                    (void**)&s.d_rfy, (void**)&s.d_rfq, (void**)&s.d_rfb, (void**)&s.d_rfe, (void**)&s.d_rfjp,
+                    (void**)&s.d_rfs, (void**)&s.d_rff};
+  for (void** b : lbufs)
+    if (*b) {
+      cudaFree(*b);
+      *b = nullptr;
+    }
+  ctx->have_prop = false;
   Mps* ms[] = {s.phi, s.eta, s.theta, s.spare};
   for (Mps* m : ms)
     if (m) {
@@ -259,6 +269,22 @@ qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
   CK(cudaMalloc(&s.d_sync, sizeof(DevSync)));
   CK(cudaMemsetAsync(s.d_sync, 0, sizeof(DevSync), ctx->stream));
   CK(cudaMemsetAsync(s.d_disc, 0, 3 * (d + 1) * sizeof(double), ctx->stream));
+  CK(cudaMalloc(&s.d_spec, (d + 1) * z.nvmax * sizeof(double)));
+  CK(cudaMalloc(&s.d_spec_len, (d + 1) * sizeof(int)));
+  CK(cudaMalloc(&s.d_prop, (d + 1) * sizeof(int)));
+  CK(cudaMalloc(&s.d_feat, (d + 1) * (size_t)kFeat * sizeof(float)));
+  CK(cudaMalloc(&s.d_y, (d + 1) * sizeof(float)));
+  CK(cudaMemsetAsync(s.d_spec_len, 0, (d + 1) * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(s.d_prop, 0, (d + 1) * sizeof(int), ctx->stream));
+  if (ctx->p.use_learned_rank) {
+    CK(cudaMalloc(&s.d_rfy, tv * sizeof(double)));
+    CK(cudaMalloc(&s.d_rfq, tv * sizeof(double)));
+    CK(cudaMalloc(&s.d_rfb, tv * sizeof(double)));
+    CK(cudaMalloc(&s.d_rfe, tv * sizeof(double)));
+    CK(cudaMalloc(&s.d_rfjp, z.nvmax * z.nvmax * sizeof(double)));
+    CK(cudaMalloc(&s.d_rfs, 4 * sizeof(double)));
+    CK(cudaMalloc(&s.d_rff, 4 * sizeof(int)));
+  }
   s.phi = new Mps();
   s.eta = new Mps();
   s.theta = new Mps();
@@ -318,7 +344,7 @@ qtt_status device_status(qtt_ctx* ctx) {
 // Jp (r x nv) / Jt (nv x r).
 qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvmax, long long ellmax, double eps,
                   int chi, int rank_cap, int* rank_out, double* Jp, double* Jt, double* disc_out,
-                  double* sigma_out);
+                  double* sigma_out, int* nsv_out = nullptr);
 
 GemmArgs gemm0();
 
@@ -411,7 +437,7 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
 //   ell <  nv: M^T = Q R, rotate the rows of R, J = Q J_R.
 qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvmax, long long ellmax, double eps,
                   int chi, int rank_cap, int* rank_out, double* Jp, double* Jt, double* disc_out,
-                  double* sigma_out) {
+                  double* sigma_out, int* nsv_out) {
   Workspace& s = ctx->ws;
   const long long ldv = ctx->ws_nvmax;  // R / J leading dimension
   if (nvmax > ldv || ellmax * nvmax > s.tv)
@@ -430,7 +456,8 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
                          ctx->stream));
       CKS(jacobi_any(ctx, s.d_tq, ellmax, nv, ell, nvmax, ellmax, s.d_jv, ldv, s.d_norm));
     }
-    KL(KC_POST, svd_post(ctx, s.d_norm, nv, len, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt));
+    KL(KC_POST, svd_post(ctx, s.d_norm, nv, len, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt,
+                         nsv_out));
     return QTT_OK;
   }
   if (ellmax > ldv) return fail(QTT_EINVAL, "internal: SVD larger than the workspace");
@@ -455,7 +482,8 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
   g.sci = dconst(ldv);
   g.scj = dconst(1);
   KL(KC_GEMM, gemm_any(ctx, g, ellmax, nvmax, 1, 1));
-  KL(KC_POST, svd_post(ctx, s.d_norm, dptr(kq), ell, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt));
+  KL(KC_POST, svd_post(ctx, s.d_norm, dptr(kq), ell, nv, s.d_jv, ldv, eps, chi, rank_cap, rank_out, sig, disc_out, Jp, Jt,
+                       nsv_out));
   return QTT_OK;
 }
 
@@ -647,8 +675,105 @@ qtt_status form_sum(qtt_ctx* ctx, const std::vector<std::pair<double, const Mps*
 }
 
 // ------------------------------------------------------------------ round
+// Range finder for bond k of the round's SVD sweep (the learned form).  The
+// matrix X (l x m, l = q_k, m = 2 r_{k+1}) is held as m vectors of length l
+// in Tv.  With Omega = the top-left l x ks block of the sketch matrix:
+//   Y = X^T Omega (ks vectors of length m), Y = Q R (thin Q, m x ks),
+//   B = Q^T X^T (ks vectors of length l), rho^2 = ||X^T - Q B||_F^2 (FP64),
+//   SVD of B by the rounding rule: B^T J = U S with J = the left singular
+//   vectors of B; the new core k is (Q J_r)^T.
+// Writes the accept flag to d_rff[0] (1 accept, 0 reject, 2 not attempted);
+// the core and rank are only meaningful when accepted.
+qtt_status rf_bond(qtt_ctx* ctx, const Mps* th, Mps* out, int k, int ks, long long nvmax, long long ellmax) {
+  Workspace& s = ctx->ws;
+  const int d = ctx->d;
+  const int* q_p = th->ranks + k;
+  const int* r2_p = out->ranks + k + 1;
+  int* r_p = out->ranks + k;
+  const Dim nv = dptr(r2_p, 2), ell = dptr(q_p);
+  const long long ld_om = ctx->sketch_cols;
+  // Y[j][c] = sum_l Omega[l][j] Tv[c][l]
+  GemmArgs g = gemm0();
+  g.A = ctx->sketch;
+  g.B = s.d_tv;
+  g.C = s.d_rfy;
+  g.M = dconst(ks);
+  g.N = nv;
+  g.K = ell;
+  g.sai = dconst(1);
+  g.sak = dconst(ld_om);
+  g.sbk = dconst(1);
+  g.sbj = ell;
+  g.sci = nv;
+  g.scj = dconst(1);
+  KL(KC_GEMM, gemm_any(ctx, g, ks, nvmax, 1, 1));
+  // thin Q of Y (m x ks, row-major); R is not needed
+  KL(KC_QR, qr_any(ctx, s.d_rfy, nv, s.d_tq, nvmax, nv, dconst(ks), ks, s.d_rv, false, s.d_rfq, s.d_rff + 1, ks,
+                   nvmax));
+  // B[j][l] = sum_c Q[c][j] Tv[c][l]
+  GemmArgs b = gemm0();
+  b.A = s.d_rfq;
+  b.B = s.d_tv;
+  b.C = s.d_rfb;
+  b.M = dconst(ks);
+  b.N = ell;
+  b.K = nv;
+  b.sai = dconst(1);
+  b.sak = dconst(ks);
+  b.sbk = ell;
+  b.sbj = dconst(1);
+  b.sci = ell;
+  b.scj = dconst(1);
+  KL(KC_GEMM, gemm_any(ctx, b, ks, ellmax, 1, 1));
+  // E = Tv - Q B in FP64, rho^2 = |E|^2, |X|^2
+  KL(KC_COPY, copy2d(s.d_tv, s.d_rfe, nv, ell, ell, dconst(1), ell, dconst(1), nvmax * ellmax, 1.0, ctx->stream));
+  GemmArgs e = gemm0();
+  e.A = s.d_rfq;
+  e.B = s.d_rfb;
+  e.C = s.d_rfe;
+  e.M = nv;
+  e.N = ell;
+  e.K = dconst(ks);
+  e.sai = dconst(ks);
+  e.sak = dconst(1);
+  e.sbk = ell;
+  e.sbj = dconst(1);
+  e.sci = ell;
+  e.scj = dconst(1);
+  e.alpha = -1.0;
+  e.beta = 1.0;
+  KL(KC_GEMM, gemm_f64(e, nvmax, ellmax, 1, 1, ctx->stream));
+  KL(KC_OTHER, sumsq(s.d_rfe, ell, nv, ell, s.d_rfs + 0, ctx->stream));
+  KL(KC_OTHER, sumsq(s.d_tv, ell, nv, ell, s.d_rfs + 1, ctx->stream));
+  // SVD of B (ks vectors of length l) by the rounding rule
+  double* sig = s.d_spec + (long long)k * ctx->ws_nvmax;
+  CKS(svd_vm(ctx, s.d_rfb, dconst(ks), ell, ks, ellmax, ctx->p.eps, ctx->p.chi_max, out->cap[k], r_p, s.d_rfjp,
+             nullptr, nullptr, sig, s.d_spec_len + k));
+  KL(KC_OTHER, rf_accept(sig, s.d_spec_len + k, r_p, ks, r2_p, q_p, 2, ctx->p.eps, ctx->p.chi_max, ctx->tau,
+                         s.d_rfs + 0, s.d_rfs + 1, s.d_rff, s.d_disc + 2 * (d + 1) + k, ctx->stream));
+  // core k (r x m) = J_r^T Q^T: core[i][c] = sum_j Jp[i][j] Q[c][j]
+  GemmArgs c = gemm0();
+  c.A = s.d_rfjp;
+  c.B = s.d_rfq;
+  c.C = out->core(k);
+  c.M = dptr(r_p);
+  c.N = nv;
+  c.K = dconst(ks);
+  c.sai = dconst(ks);
+  c.sak = dconst(1);
+  c.sbk = dconst(1);
+  c.sbj = dconst(ks);
+  c.sci = nv;
+  c.scj = dconst(1);
+  KL(KC_GEMM, gemm_any(ctx, c, std::min<long long>(out->cap[k], ks), nvmax, 1, 1));
+  return QTT_OK;
+}
+
 // out = round(theta): QR sweep 0 -> d-1, then truncated-SVD sweep d-1 -> 1
-// (Sec. 4.3).  theta is overwritten.
+// (Sec. 4.3).  theta is overwritten.  Every bond's singular values go to the
+// spectrum log.  In the learned form, a bond with a proposed rank first tries
+// the range finder (rf_bond) and keeps its result when the exact check
+// accepts it; otherwise it takes the full SVD.
 qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
   Workspace& s = ctx->ws;
   const int d = ctx->d;
@@ -690,6 +815,13 @@ qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
     }
     KL(KC_GEMM, gemm_any(ctx, g, std::min<long long>(2LL * cap[k], cap[k + 1]), cap[k + 2], 2, 1));
   }
+  const bool learned = ctx->p.use_learned_rank && ctx->sketch && ctx->have_prop && s.d_rfy;
+  std::vector<int> prop;
+  if (learned) {
+    prop.resize(d + 1);
+    CK(cudaMemcpyAsync(prop.data(), s.d_prop, (d + 1) * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   for (int k = d - 1; k >= 1; --k) {
     const int* q_p = th->ranks + k;  // rows of core k
     const int* r2_p = out->ranks + k + 1;
@@ -697,8 +829,24 @@ qtt_status tt_round(qtt_ctx* ctx, Mps* th, Mps* out) {
     const Dim nv = dptr(r2_p, 2), ell = dptr(q_p);
     const long long nvmax = 2LL * out->cap[k + 1];
     const long long ellmax = std::min<long long>(cap[k], p2(k));  // q_k <= 2^k after the QR sweep
-    CKS(svd_vm(ctx, s.d_tv, nv, ell, nvmax, ellmax, ctx->p.eps, ctx->p.chi_max, out->cap[k], r_p, out->core(k),
-               nullptr, s.d_disc + 2 * (d + 1) + k, nullptr));
+    bool done = false;
+    if (learned && prop[k] > 0) {
+      const int ks = prop[k] + ctx->oversample;
+      if (ks < std::min(nvmax, ellmax) && ks <= ctx->sketch_cols && ellmax <= ctx->sketch_rows) {
+        CKS(rf_bond(ctx, th, out, k, ks, nvmax, ellmax));
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, s.d_rff, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (flag != 2) ++ctx->rf_attempts;
+        if (flag == 1) {
+          ++ctx->rf_accepts;
+          done = true;
+        }
+      }
+    }
+    if (!done)
+      CKS(svd_vm(ctx, s.d_tv, nv, ell, nvmax, ellmax, ctx->p.eps, ctx->p.chi_max, out->cap[k], r_p, out->core(k),
+                 nullptr, s.d_disc + 2 * (d + 1) + k, s.d_spec + (long long)k * ctx->ws_nvmax, s.d_spec_len + k));
     // W1 (r x q_k) = Jp Tv
     GemmArgs g = gemm0();
     g.A = out->core(k);
@@ -786,6 +934,31 @@ qtt_status tt_svd(qtt_ctx* ctx, const double* grid_dev, bool square, double eps,
   return QTT_OK;
 }
 
+}  // namespace
+
+struct qtt_mlp {
+  qtt::MlpDev dev;
+  cudaStream_t stream = nullptr;
+  int t = 0;  // Adam steps taken
+};
+
+namespace {
+
+// Features of bonds 1..d-1 from the last round's spectra and the ranks of
+// psi (its result), the network's outputs, and the proposals for the next
+// step's round.
+qtt_status propose_ranks(qtt_ctx* ctx, const Mps* psi) {
+  Workspace& s = ctx->ws;
+  const int nb = ctx->d - 1;
+  if (nb < 1) return QTT_OK;
+  KL(KC_OTHER, rank_features(s.d_spec, ctx->ws_nvmax, s.d_spec_len, psi->ranks, nb, ctx->p.eps, ctx->p.chi_max,
+                             ctx->d, s.d_feat, ctx->stream));
+  KL(KC_OTHER, mlp_forward(ctx->mlp->dev, s.d_feat, nb, s.d_y, ctx->stream));
+  KL(KC_OTHER, propose(s.d_y, nb, ctx->p.chi_max, s.d_prop, ctx->stream));
+  ctx->have_prop = true;
+  return QTT_OK;
+}
+
 bool cuda_ok_device() {
   int n = 0;
   return cudaGetDeviceCount(&n) == cudaSuccess && n > 0;
@@ -810,7 +983,7 @@ qtt_status qtt_ctx_create(const qtt_params* p, void* stream, qtt_ctx** out) {
   if (!(p->eps >= 0.0 && p->eps < 1.0)) return fail(QTT_EINVAL, "eps must be in [0, 1)");
   if (p->chi_zip < 0 || p->chi_zip > 1024 || p->chi_c < 0 || p->chi_c > 1024)
     return fail(QTT_EINVAL, "chi_zip / chi_c must be in 0..1024");
-  if (p->use_learned_rank != 0) return fail(QTT_EINVAL, "use_learned_rank is reserved");
+  if (p->use_learned_rank != 0 && p->use_learned_rank != 1) return fail(QTT_EINVAL, "use_learned_rank must be 0 or 1");
   if (!cuda_ok_device()) return fail(QTT_ECUDA, "no CUDA device");
   qtt_ctx* c = new qtt_ctx();
   c->p = *p;
@@ -1030,6 +1203,13 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
   CKS(ensure_ws(ctx, L->w, rc));
   Caps c = step_caps(ctx, L->w, rc);
   Workspace& s = ctx->ws;
+  if (!ctx->pending_prop.empty()) {
+    CK(cudaMemcpyAsync(s.d_prop, ctx->pending_prop.data(), (ctx->d + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pending_prop.clear();
+    ctx->have_prop = true;
+  }
   struct MpScope {  // the reduced-precision form applies inside the step only
     qtt_ctx* c;
     explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec == QTT_FP32); }
@@ -1039,9 +1219,148 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
   CKS(zipup_C(ctx, c2, rc, s.phi, s.eta, c));
   CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta));
   CKS(tt_round(ctx, s.theta, prev));
+  ctx->have_prop = false;  // proposals are for one step
+  if (ctx->p.use_learned_rank && ctx->mlp) CKS(propose_ranks(ctx, prev));
   // prev now holds u^{k+1}: exchange buffers so that prev = u^k, cur = u^{k+1}
   std::swap(prev->data, cur->data);
   std::swap(prev->ranks, cur->ranks);
+  return QTT_OK;
+}
+
+// ------------------------------------------------------------ learned form
+int qtt_mlp_param_count(void) { return (int)kParams; }
+
+void qtt_mlp_destroy(qtt_mlp* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  float* bufs[] = {m->dev.p, m->dev.g, m->dev.m, m->dev.v, m->dev.a1, m->dev.a2, m->dev.d1, m->dev.d2, m->dev.y, m->dev.dy};
+  for (float* b : bufs)
+    if (b) cudaFree(b);
+  delete m;
+}
+
+qtt_status qtt_mlp_create(const float* params, int max_batch, void* stream, qtt_mlp** out) {
+  if (!params || !out || max_batch < 1) return fail(QTT_EINVAL, "bad MLP arguments");
+  *out = nullptr;
+  if (!cuda_ok_device()) return fail(QTT_ECUDA, "no CUDA device");
+  qtt_mlp* m = new qtt_mlp();
+  m->stream = (cudaStream_t)stream;
+  m->dev.max_batch = max_batch;
+  const size_t pb = kParams * sizeof(float), ab = (size_t)max_batch * kWidth * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  float** pbufs[] = {&m->dev.p, &m->dev.g, &m->dev.m, &m->dev.v};
+  for (float** b : pbufs)
+    if (e == cudaSuccess) e = cudaMalloc(b, pb);
+  float** abufs[] = {&m->dev.a1, &m->dev.a2, &m->dev.d1, &m->dev.d2};
+  for (float** b : abufs)
+    if (e == cudaSuccess) e = cudaMalloc(b, ab);
+  if (e == cudaSuccess) e = cudaMalloc(&m->dev.y, max_batch * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->dev.dy, max_batch * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->dev.p, params, pb, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->dev.g, 0, pb, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->dev.m, 0, pb, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->dev.v, 0, pb, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    qtt_mlp_destroy(m);
+    return fail(e == cudaErrorMemoryAllocation ? QTT_ENOMEM : QTT_ECUDA, cudaGetErrorString(e));
+  }
+  *out = m;
+  return QTT_OK;
+}
+
+qtt_status qtt_mlp_forward(qtt_mlp* m, const float* X, int n, float* y) {
+  if (!m || !X || !y || n < 0) return fail(QTT_EINVAL, "bad MLP forward arguments");
+  if (n > m->dev.max_batch) return fail(QTT_EINVAL, "batch larger than the network's max_batch");
+  if (n == 0) return QTT_OK;
+  CK(mlp_forward(m->dev, X, n, y, m->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_mlp_grad(qtt_mlp* m, const float* X, const float* t, int n, float* loss, float* grad) {
+  if (!m || !X || !t || n < 1) return fail(QTT_EINVAL, "bad MLP gradient arguments");
+  if (n > m->dev.max_batch) return fail(QTT_EINVAL, "batch larger than the network's max_batch");
+  CK(mlp_grad(m->dev, X, t, n, loss, m->stream));
+  if (grad) CK(cudaMemcpyAsync(grad, m->dev.g, kParams * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_mlp_adam_step(qtt_mlp* m, float lr, float beta1, float beta2, float eps) {
+  if (!m) return fail(QTT_EINVAL, "null network");
+  if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return fail(QTT_EINVAL, "bad Adam hyper-parameters");
+  ++m->t;
+  CK(mlp_adam(m->dev, m->t, lr, beta1, beta2, eps, m->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_mlp_get_params(qtt_mlp* m, float* params) {
+  if (!m || !params) return fail(QTT_EINVAL, "null argument");
+  CK(cudaMemcpyAsync(params, m->dev.p, kParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_rank_features(const double* S, int lds, const int* len, const int* ranks, int nb, double eps, int chi,
+                             int d, float* X, void* stream) {
+  if (!S || !len || !ranks || !X || nb < 0 || nb > d - 1 || lds < 1 || chi < 1 || d < 2)
+    return fail(QTT_EINVAL, "bad feature arguments");
+  CK(rank_features(S, lds, len, ranks, nb, eps, chi, d, X, (cudaStream_t)stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_step_features(qtt_ctx* ctx, const qtt_mps* psi, float* X) {
+  if (!ctx || !psi || !X) return fail(QTT_EINVAL, "null argument");
+  if (!ctx->ws_ready) return fail(QTT_EINVAL, "no step has run on this context");
+  CK(rank_features(ctx->ws.d_spec, ctx->ws_nvmax, ctx->ws.d_spec_len, psi->ranks, ctx->d - 1, ctx->p.eps,
+                   ctx->p.chi_max, ctx->d, X, ctx->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_set_rank_model(qtt_ctx* ctx, qtt_mlp* m, const double* sketch, int rows, int cols, int oversample) {
+  if (!ctx) return fail(QTT_EINVAL, "null context");
+  if (!sketch) {
+    ctx->mlp = nullptr;
+    ctx->sketch = nullptr;
+    ctx->have_prop = false;
+    return QTT_OK;
+  }
+  if (!ctx->p.use_learned_rank) return fail(QTT_EINVAL, "the context was created with use_learned_rank = 0");
+  if (rows < 1 || cols < 1 || oversample < 0) return fail(QTT_EINVAL, "bad sketch arguments");
+  if (m && m->dev.max_batch < ctx->d) return fail(QTT_EINVAL, "the network's max_batch must be >= 2n");
+  ctx->mlp = m;
+  ctx->sketch = sketch;
+  ctx->sketch_rows = rows;
+  ctx->sketch_cols = cols;
+  ctx->oversample = oversample;
+  ctx->have_prop = false;
+  return QTT_OK;
+}
+
+qtt_status qtt_get_proposals(qtt_ctx* ctx, int* prop) {
+  if (!ctx || !prop) return fail(QTT_EINVAL, "null argument");
+  if (!ctx->ws_ready || !ctx->have_prop) {
+    for (int k = 0; k <= ctx->d; ++k) prop[k] = 0;
+    return QTT_OK;
+  }
+  CK(cudaMemcpyAsync(prop, ctx->ws.d_prop, (ctx->d + 1) * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_set_proposals(qtt_ctx* ctx, const int* prop) {
+  if (!ctx || !prop) return fail(QTT_EINVAL, "null argument");
+  if (!ctx->p.use_learned_rank) return fail(QTT_EINVAL, "the context was created with use_learned_rank = 0");
+  for (int k = 0; k <= ctx->d; ++k)
+    if (prop[k] < 0 || prop[k] > ctx->p.chi_max) return fail(QTT_EINVAL, "proposals must be in 0..chi_max");
+  ctx->pending_prop.assign(prop, prop + ctx->d + 1);
+  return QTT_OK;
+}
+
+qtt_status qtt_learned_stats(qtt_ctx* ctx, long* attempts, long* accepts) {
+  if (!ctx || !attempts || !accepts) return fail(QTT_EINVAL, "null argument");
+  *attempts = (long)ctx->rf_attempts;
+  *accepts = (long)ctx->rf_accepts;
   return QTT_OK;
 }
 

@@ -200,6 +200,22 @@ struct Workspace {
   double* d_disc = nullptr;   // discarded weights per (phase, bond)
   int* d_ints = nullptr;      // scratch ints (ranks of temporaries)
   DevSync* d_sync = nullptr;
+  // learned form: spectra of the last round (row k = bond k, ws_nvmax wide),
+  // their lengths, the proposed ranks, features and network outputs
+  double* d_spec = nullptr;
+  int* d_spec_len = nullptr;
+  int* d_prop = nullptr;
+  float* d_feat = nullptr;
+  float* d_y = nullptr;
+  // range finder (allocated when the context uses learned ranks): sketch Y,
+  // its thin Q, B = Q^T X^T, residual E, kept rotations, scalars, flags
+  double* d_rfy = nullptr;
+  double* d_rfq = nullptr;
+  double* d_rfb = nullptr;
+  double* d_rfe = nullptr;
+  double* d_rfjp = nullptr;
+  double* d_rfs = nullptr;
+  int* d_rff = nullptr;
   Mps* phi = nullptr;
   Mps* eta = nullptr;
   Mps* theta = nullptr;
@@ -223,6 +239,8 @@ struct Prof {
 };
 }  // namespace qtt
 
+struct qtt_mlp;
+
 struct qtt_ctx {
   qtt_params p{};
   int d = 0;
@@ -236,6 +254,15 @@ struct qtt_ctx {
   bool use_mp = false;      // inside a reduced-precision step: FP32 contractions and QR, mixed SVD
   long long ws_nvmax = 0;   // widest SVD (vectors) the workspace holds
   long long ws_ellmax = 0;  // longest vector of a step SVD
+  // learned form (Sec. 4.3 rule kept as the judge)
+  qtt_mlp* mlp = nullptr;          // rank model (not owned)
+  const double* sketch = nullptr;  // Gaussian test matrix, row-major rows x cols (not owned)
+  long long sketch_rows = 0, sketch_cols = 0;
+  int oversample = 16;
+  double tau = 0.05;
+  bool have_prop = false;          // d_prop holds proposals from the previous step
+  std::vector<int> pending_prop;   // proposals set by the caller for the next step
+  long long rf_attempts = 0, rf_accepts = 0;
 };
 
 namespace qtt {
@@ -286,8 +313,9 @@ int* jacobi_log_slot(qtt_ctx* ctx);
 // cnt rotated vectors with norms; len: their length (min(cnt, len) singular
 // values exist); jlen: length of a row of J (the number of input vectors);
 // rank_cap: the destination capacity (a larger rank is clamped and reported).
+// nsv_out (optional): min(cnt, len), the number of singular values.
 cudaError_t svd_post(qtt_ctx* ctx, const double* norms, Dim cnt, Dim len, Dim jlen, const double* J, long long ldj,
                      double eps, int chi, int rank_cap, int* rank_out, double* sigma_out, double* disc_out,
-                     double* Jp, double* Jt);
+                     double* Jp, double* Jt, int* nsv_out = nullptr);
 
 }  // namespace qtt

@@ -79,22 +79,35 @@ _SIGS = {
     "qtt_batch_create": [ctypes.POINTER(qtt_params), _I, _PI, _P, ctypes.POINTER(_P)],
     "qtt_step_batched": [_P, _P, _P, _D, ctypes.POINTER(_P), ctypes.POINTER(_P), _PL, _PD],
     "qtt_profile_read": [_P, ctypes.POINTER(qtt_profile)],
+    "qtt_mlp_create": [ctypes.POINTER(ctypes.c_float), _I, _P, ctypes.POINTER(_P)],
+    "qtt_mlp_forward": [_P, _P, _I, _P],
+    "qtt_mlp_grad": [_P, _P, _P, _I, _P, _P],
+    "qtt_mlp_adam_step": [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float],
+    "qtt_mlp_get_params": [_P, ctypes.POINTER(ctypes.c_float)],
+    "qtt_rank_features": [_P, _I, _P, _P, _I, _D, _I, _I, _P, _P],
+    "qtt_step_features": [_P, _P, _P],
+    "qtt_set_rank_model": [_P, _P, _P, _I, _I, _I],
+    "qtt_set_proposals": [_P, _PI],
+    "qtt_get_proposals": [_P, _PI],
+    "qtt_learned_stats": [_P, _PL, _PL],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
-for _name in ("qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_batch_destroy"):
+for _name in ("qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_batch_destroy", "qtt_mlp_destroy"):
     getattr(_lib, _name).argtypes = [_P]
     getattr(_lib, _name).restype = None
 _lib.qtt_batch_ctx.argtypes = [_P, _I]
 _lib.qtt_batch_ctx.restype = _P
+_lib.qtt_mlp_param_count.argtypes = []
+_lib.qtt_mlp_param_count.restype = _I
 _lib.qtt_last_error.argtypes = []
 _lib.qtt_last_error.restype = ctypes.c_char_p
 
 # every symbol include/qtt.h declares
 EXPORTED = sorted(list(_SIGS) + ["qtt_ctx_destroy", "qtt_mps_destroy", "qtt_mpo_destroy", "qtt_last_error",
-                                  "qtt_batch_destroy", "qtt_batch_ctx"])
+                                  "qtt_batch_destroy", "qtt_batch_ctx", "qtt_mlp_destroy", "qtt_mlp_param_count"])
 
 
 def _check(st: int, where: str) -> None:
@@ -104,10 +117,20 @@ def _check(st: int, where: str) -> None:
 
 def _dev_ptr(t, dtype_name: str = "float64") -> int:
     import torch
-    want = {"float64": torch.float64, "int64": torch.int64}[dtype_name]
+    want = {"float64": torch.float64, "int64": torch.int64, "float32": torch.float32,
+            "int32": torch.int32}[dtype_name]
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != want or not t.is_contiguous():
         raise TypeError(f"expected a contiguous CUDA {dtype_name} tensor")
     return t.data_ptr()
+
+
+def _ptr(t) -> _P:
+    """Device pointer of a contiguous CUDA tensor of any of the accepted types."""
+    import torch
+    names = {torch.float64: "float64", torch.float32: "float32", torch.int32: "int32", torch.int64: "int64"}
+    if not isinstance(t, torch.Tensor) or t.dtype not in names:
+        raise TypeError("expected a CUDA tensor of float64, float32, int32 or int64")
+    return _P(_dev_ptr(t, names[t.dtype]))
 
 
 class Ctx:
@@ -158,13 +181,14 @@ def qtt_last_error() -> str:
 
 def qtt_ctx_create(n: int, order: str = "interleaved", bc: str = "periodic", chi_max: int = 32,
                    eps: float = 1e-10, chi_zip: int = 0, eps_zip: float = 0.0, chi_c: int = 0,
-                   eps_c: float = 0.0, prec: str = "fp64", stream=None) -> Ctx:
+                   eps_c: float = 0.0, prec: str = "fp64", stream=None, learned: bool = False) -> Ctx:
     """Context on the current CUDA device; ``stream`` is a torch.cuda.Stream
     (default: torch's current stream)."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, chi_zip, eps_zip, chi_c, eps_c, 0)
+    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, chi_zip, eps_zip, chi_c, eps_c,
+                   int(learned))
     h = _P()
     _check(_lib.qtt_ctx_create(ctypes.byref(p), _P(stream.cuda_stream), ctypes.byref(h)), "qtt_ctx_create")
     return Ctx(h.value, p)
@@ -402,6 +426,106 @@ def qtt_step_batched(batch: Batch, L: Mpo, c2: Mps, lambda2: float, prev: list, 
         a = (ctypes.c_double * n)(*[float(v) for v in amp])
     _check(_lib.qtt_step_batched(batch.h, L.h, c2.h, lambda2, P, C, s, a), "qtt_step_batched")
     # the library exchanged each pair's buffers; the handles keep their roles
+
+
+class Mlp:
+    """Handle of a qtt_mlp (the rank-proposal network) and its stream."""
+
+    def __init__(self, handle: int, stream):
+        self.h = handle
+        self.stream = stream
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qtt_mlp_destroy(self.h)
+            self.h = None
+
+
+def qtt_mlp_param_count() -> int:
+    return int(_lib.qtt_mlp_param_count())
+
+
+def qtt_mlp_create(params, max_batch: int, stream=None) -> Mlp:
+    """params: host float32 array of qtt_mlp_param_count() values."""
+    import numpy as np
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != qtt_mlp_param_count():
+        raise ValueError("wrong parameter count")
+    h = _P()
+    _check(_lib.qtt_mlp_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(max_batch),
+                               _P(stream.cuda_stream), ctypes.byref(h)), "qtt_mlp_create")
+    return Mlp(h.value, stream)
+
+
+def qtt_mlp_destroy(m: Mlp) -> None:
+    m.__del__()
+
+
+def qtt_mlp_forward(m: Mlp, X, y) -> None:
+    """X: float32 CUDA tensor n x 40; y: float32 CUDA tensor n."""
+    _check(_lib.qtt_mlp_forward(m.h, _ptr(X), int(X.shape[0]), _ptr(y)), "qtt_mlp_forward")
+
+
+def qtt_mlp_grad(m: Mlp, X, t, loss=None, grad=None) -> None:
+    _check(_lib.qtt_mlp_grad(m.h, _ptr(X), _ptr(t), int(X.shape[0]), _ptr(loss) if loss is not None else None,
+                             _ptr(grad) if grad is not None else None), "qtt_mlp_grad")
+
+
+def qtt_mlp_adam_step(m: Mlp, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    _check(_lib.qtt_mlp_adam_step(m.h, lr, beta1, beta2, eps), "qtt_mlp_adam_step")
+
+
+def qtt_mlp_get_params(m: Mlp):
+    import numpy as np
+    out = np.empty(qtt_mlp_param_count(), dtype=np.float32)
+    _check(_lib.qtt_mlp_get_params(m.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "qtt_mlp_get_params")
+    return out
+
+
+def qtt_rank_features(S, lens, ranks, nb: int, eps: float, chi: int, d: int, X, stream=None) -> None:
+    """S: float64 CUDA tensor (rows x lds); lens, ranks: int32 CUDA tensors;
+    X: float32 CUDA tensor nb x 40."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.qtt_rank_features(_ptr(S), int(S.shape[1]), _ptr(lens), _ptr(ranks), nb, eps, chi, d, _ptr(X),
+                                  _P(stream.cuda_stream)), "qtt_rank_features")
+
+
+def qtt_step_features(psi: Mps, X) -> None:
+    _check(_lib.qtt_step_features(psi.ctx.h, psi.h, _ptr(X)), "qtt_step_features")
+
+
+def qtt_set_rank_model(ctx: Ctx, mlp, sketch, oversample: int = 16) -> None:
+    """mlp: Mlp or None; sketch: float64 CUDA tensor rows x cols (kept alive
+    by the caller) or None to turn the learned rounding off."""
+    ctx._sketch = sketch
+    ctx._mlp = mlp
+    if sketch is None:
+        _check(_lib.qtt_set_rank_model(ctx.h, None, None, 0, 0, 0), "qtt_set_rank_model")
+        return
+    _check(_lib.qtt_set_rank_model(ctx.h, mlp.h if mlp is not None else None, _ptr(sketch), int(sketch.shape[0]),
+                                   int(sketch.shape[1]), int(oversample)), "qtt_set_rank_model")
+
+
+def qtt_set_proposals(ctx: Ctx, prop) -> None:
+    a = (ctypes.c_int * (ctx.d + 1))(*[int(x) for x in prop])
+    _check(_lib.qtt_set_proposals(ctx.h, a), "qtt_set_proposals")
+
+
+def qtt_get_proposals(ctx: Ctx) -> list:
+    a = (ctypes.c_int * (ctx.d + 1))()
+    _check(_lib.qtt_get_proposals(ctx.h, a), "qtt_get_proposals")
+    return list(a)
+
+
+def qtt_learned_stats(ctx: Ctx) -> tuple:
+    a, b = ctypes.c_long(), ctypes.c_long()
+    _check(_lib.qtt_learned_stats(ctx.h, ctypes.byref(a), ctypes.byref(b)), "qtt_learned_stats")
+    return a.value, b.value
 
 
 def qtt_profile_start(ctx: Ctx, timing: bool = False, log_svd: bool = False) -> None:

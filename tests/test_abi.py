@@ -55,7 +55,7 @@ def _params(lib, **kw):
 
 
 @pytest.mark.parametrize("bad", [dict(n=0), dict(n=15), dict(order=7), dict(bc=3), dict(chi_max=0),
-                                 dict(eps=-1.0), dict(eps=1.5), dict(prec=9), dict(use_learned_rank=1),
+                                 dict(eps=-1.0), dict(eps=1.5), dict(prec=9), dict(use_learned_rank=2),
                                  dict(chi_zip=-1)])
 def test_ctx_create_rejects_bad_params_without_a_device(lib, bad):
     p = _params(lib, **bad)
