@@ -139,6 +139,13 @@ qtt_status qtt_laplacian_mpo(qtt_ctx* ctx, qtt_mpo** out);
 qtt_status qtt_mpo_bonds(const qtt_mpo* L, int* bonds_out);
 void qtt_mpo_destroy(qtt_mpo* L);
 
+/* Checkpoint of a state: file = 8 bytes "QTTMPS1\0", int32 d, int32
+ * ranks[d+1], then the cores [r_k][2][r_{k+1}] as FP64, little-endian.  Load
+ * returns QTT_EINVAL for another grid size or a rank above the context's
+ * capacity. */
+qtt_status qtt_mps_save(qtt_ctx* ctx, const qtt_mps* psi, const char* path);
+qtt_status qtt_mps_load(qtt_ctx* ctx, const char* path, qtt_mps** out);
+
 /* ------------------------------------------------------------------- step */
 
 /* psi <- round(psi + amp * e_(ix,iz)): a rank-1 product-state add (the

@@ -2,6 +2,7 @@
 // time step (Eq. 17) as a sequence of launches on the context stream with
 // every bond rank kept in device memory (no host synchronisation per step).
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cmath>
 #include <cstring>
@@ -1093,6 +1094,56 @@ qtt_status qtt_mps_get_cores(qtt_ctx* ctx, const qtt_mps* psi, int* ranks, doubl
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return QTT_OK;
+}
+
+// File layout: 8 bytes "QTTMPS1\0", int32 d, int32 ranks[d+1], then the
+// cores k = 0..d-1 ([r_k][2][r_{k+1}], FP64), all little-endian.
+qtt_status qtt_mps_save(qtt_ctx* ctx, const qtt_mps* psi, const char* path) {
+  if (!ctx || !psi || !path) return fail(QTT_EINVAL, "null argument");
+  const int d = psi->d;
+  std::vector<int> r(d + 1);
+  CKS(qtt_mps_ranks(ctx, psi, r.data()));
+  long long need = 0;
+  for (int k = 0; k < d; ++k) need += (long long)r[k] * 2 * r[k + 1];
+  std::vector<double> cores(std::max(need, 1LL));
+  CKS(qtt_mps_get_cores(ctx, psi, r.data(), cores.data(), (long)need));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(QTT_EINVAL, std::string("cannot open ") + path + " for writing");
+  const char magic[8] = {'Q', 'T', 'T', 'M', 'P', 'S', '1', '\0'};
+  const int32_t d32 = d;
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&d32, 4, 1, f) == 1;
+  for (int k = 0; ok && k <= d; ++k) {
+    const int32_t v = r[k];
+    ok = std::fwrite(&v, 4, 1, f) == 1;
+  }
+  if (ok && need > 0) ok = std::fwrite(cores.data(), sizeof(double), need, f) == (size_t)need;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(QTT_EINVAL, std::string("write failed: ") + path);
+  return QTT_OK;
+}
+
+qtt_status qtt_mps_load(qtt_ctx* ctx, const char* path, qtt_mps** out) {
+  if (!ctx || !path || !out) return fail(QTT_EINVAL, "null argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(QTT_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t d32 = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "QTTMPS1\0", 8) == 0 &&
+            std::fread(&d32, 4, 1, f) == 1 && d32 == ctx->d;
+  std::vector<int> r(ctx->d + 1);
+  for (int k = 0; ok && k <= ctx->d; ++k) {
+    int32_t v = 0;
+    ok = std::fread(&v, 4, 1, f) == 1 && v >= 1 && v <= (1 << 20);
+    r[k] = v;
+  }
+  long long need = 0;
+  for (int k = 0; ok && k < ctx->d; ++k) need += (long long)r[k] * 2 * r[k + 1];
+  std::vector<double> cores(std::max(need, 1LL));
+  if (ok && need > 0) ok = std::fread(cores.data(), sizeof(double), need, f) == (size_t)need;
+  std::fclose(f);
+  if (!ok) return fail(QTT_EINVAL, std::string("not an MPS file of this grid size: ") + path);
+  return qtt_mps_from_cores(ctx, r.data(), cores.data(), out);
 }
 
 static qtt_status from_dense_impl(qtt_ctx* ctx, const double* grid, int on_device, bool square, double eps, int chi,

@@ -79,6 +79,8 @@ _SIGS = {
     "qtt_batch_create": [ctypes.POINTER(qtt_params), _I, _PI, _P, ctypes.POINTER(_P)],
     "qtt_step_batched": [_P, _P, _P, _D, ctypes.POINTER(_P), ctypes.POINTER(_P), _PL, _PD],
     "qtt_profile_read": [_P, ctypes.POINTER(qtt_profile)],
+    "qtt_mps_save": [_P, _P, ctypes.c_char_p],
+    "qtt_mps_load": [_P, ctypes.c_char_p, ctypes.POINTER(_P)],
     "qtt_mlp_create": [ctypes.POINTER(ctypes.c_float), _I, _P, ctypes.POINTER(_P)],
     "qtt_mlp_forward": [_P, _P, _I, _P],
     "qtt_mlp_grad": [_P, _P, _P, _I, _P, _P],
@@ -426,6 +428,16 @@ def qtt_step_batched(batch: Batch, L: Mpo, c2: Mps, lambda2: float, prev: list, 
         a = (ctypes.c_double * n)(*[float(v) for v in amp])
     _check(_lib.qtt_step_batched(batch.h, L.h, c2.h, lambda2, P, C, s, a), "qtt_step_batched")
     # the library exchanged each pair's buffers; the handles keep their roles
+
+
+def qtt_mps_save(psi: Mps, path: str) -> None:
+    _check(_lib.qtt_mps_save(psi.ctx.h, psi.h, os.fsencode(path)), "qtt_mps_save")
+
+
+def qtt_mps_load(ctx: Ctx, path: str) -> Mps:
+    h = _P()
+    _check(_lib.qtt_mps_load(ctx.h, os.fsencode(path), ctypes.byref(h)), "qtt_mps_load")
+    return Mps(h.value, ctx)
 
 
 class Mlp:

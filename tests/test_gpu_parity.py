@@ -264,3 +264,21 @@ def test_qtt64_const_free_run_before_saturation_matches_oracle(q):
         po, co = co, O.mps_step(Lo, Co, lam2, po, co, wl.eps, wl.chi, src, float(amps[k]), n, wl.order)
     assert q.qtt_mps_ranks(cur) == O.mps_ranks(co)
     assert _rel(_dense(q, cur, N), O.mps_to_dense(co, n, wl.order)) < RTOL
+
+
+def test_mps_save_load_round_trip(q, tmp_path):
+    n, chi = 5, 16
+    ctx = q.qtt_ctx_create(n=n, chi_max=chi, eps=1e-9)
+    cores = _random_right_canonical(n, chi, 7, "interleaved")
+    psi = q.qtt_mps_from_cores(ctx, cores)
+    path = str(tmp_path / "state.qtt")
+    q.qtt_mps_save(psi, path)
+    ctx2 = q.qtt_ctx_create(n=n, chi_max=chi, eps=1e-9)
+    back = q.qtt_mps_load(ctx2, path)
+    assert q.qtt_mps_ranks(back) == O.mps_ranks(cores)
+    for a, b in zip(q.qtt_mps_get_cores(back), cores):
+        assert np.array_equal(a, b)
+    other = q.qtt_ctx_create(n=n + 1, chi_max=chi, eps=1e-9)
+    with pytest.raises(q.QttError) as e:
+        q.qtt_mps_load(other, path)
+    assert e.value.status == q.QTT_EINVAL
