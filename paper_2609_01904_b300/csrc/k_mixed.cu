@@ -156,10 +156,11 @@ __global__ void __launch_bounds__(NT32) jacobi32_cluster_kernel(const double* __
 // Block one-sided Jacobi.  The nv columns form 2*CS blocks of B columns;
 // block k lives in the shared memory of CTA k/2 (slot k%2).  A sweep is a
 // round-robin tournament over the blocks: in each of its 2*CS-1 block rounds
-// CTA r copies its pair of blocks into a local working area, performs one
-// full local sweep over their 2B columns (2B-1 rounds of B disjoint pairs,
-// one warp per pair, separated by __syncthreads only), and writes the blocks
-// back.  One cluster barrier per block round instead of one per pair round.
+// CTA r copies its pair of blocks into a local working area, rotates their
+// pairs (one warp per pair, rounds of B disjoint pairs separated by
+// __syncthreads only: all 2B-1 rounds of the 2B columns in block round 0, the
+// B rounds of cross pairs after), and writes the blocks back.  One cluster
+// barrier per block round instead of one per pair round.
 template <int EA, int EJ, int B>
 __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
                                                               Dim m_d, double* __restrict__ Jout, long long ldj,
@@ -214,10 +215,19 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
       }
       __syncthreads();
       // full local sweep over the 2B columns
-      for (int lr = 0; lr < W - 1; ++lr) {
+      // block round 0 meets every block once: a full local sweep there covers
+      // all pairs inside blocks; the other rounds rotate only the B x B pairs
+      // across their two blocks (round s pairs column w of the first block
+      // with column (w + s) mod B of the second), so each pair is visited
+      // once per sweep
+      const int nlr = t == 0 ? W - 1 : B;
+      for (int lr = 0; lr < nlr; ++lr) {
         int i, j;
         const int q = warp, R = W - 1;
-        if (q == 0) {
+        if (t != 0) {
+          i = q;
+          j = B + (q + lr) % B;
+        } else if (q == 0) {
           i = R;
           j = lr;
         } else {
