@@ -396,6 +396,240 @@ __global__ void row_norms_kernel(const double* W, long long ldw, Dim n_d, Dim m_
   }
 }
 
+// Householder QR with column pivoting (Businger & Golub 1965) of a small
+// matrix A (nr x nc, nr <= MR) in one thread-block cluster, FP32, for the
+// preconditioned Jacobi of the mixed SVD (Drmac & Veselic 2008): the rows of
+// R1 in A P = Q1 R1 are graded, and one-sided Jacobi on them needs far fewer
+// sweeps than on the columns of an unpivoted R.  A[a][i] = Ain[a * lda + i]
+// (A is the transpose of a column-major R0).  Column i lives in the shared
+// memory of CTA i % CS; a step is one cluster barrier to publish every CTA's
+// best remaining norm, one to publish the reflector, and a warp per column
+// applying it and recomputing that column's remaining norm.  Outputs: R1
+// (k1 x nc, pivoted column order) row-major at R1 (row stride ldr1), the thin
+// Q1 (nr x k1) row-major at Q1 (row stride ldq), k1 = min(nr, nc) at *k1_out.
+// Vg: global scratch of k1 * MR floats for the reflectors.
+template <int MR>
+__global__ void __launch_bounds__(NT32) qrcp_cluster_kernel(const double* __restrict__ Ain, long long lda,
+                                                            Dim nr_d, Dim nc_d, int cpc, double* R1, long long ldr1,
+                                                            double* Q1, long long ldq, float* Vg, int* k1_out) {
+  constexpr int PER = MR / 32;  // rows per lane
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks();
+  extern __shared__ float smf[];
+  float* col = smf;                              // cpc columns of MR floats
+  float* nrm = col + (long long)cpc * MR;        // remaining squared norms (-1: chosen)
+  float* s_v = nrm + cpc;                        // reflector of the current step
+  float* s_tau = s_v + MR;                       // tau of every step
+  int* s_piv = reinterpret_cast<int*>(s_tau + MR);  // logical -> physical column (<= NT32 columns)
+  int* s_pos = s_piv + NT32;                     // physical -> logical
+  __shared__ float s_cval, s_btau;
+  __shared__ int s_cidx, s_p;
+  const int nr = (int)dv(nr_d), nc = (int)dv(nc_d), k1 = nr < nc ? nr : nc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT32 / 32;
+
+  for (int sl = warp; sl < cpc; sl += nw) {
+    const int c = rank + sl * CS;
+    float s2 = 0.f;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int a = lane + 32 * t;
+      const float x = (c < nc && a < nr) ? (float)Ain[(long long)a * lda + c] : 0.f;
+      col[sl * MR + a] = x;
+      s2 = fmaf(x, x, s2);
+    }
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) nrm[sl] = c < nc ? s2 : -1.f;
+  }
+  __syncthreads();
+
+  for (int j = 0; j < k1; ++j) {
+    // this CTA's best remaining column (ties: smaller index)
+    if (warp == 0) {
+      float bv = -1.f;
+      int bi = -1;
+      for (int sl = lane; sl < cpc; sl += 32)
+        if (nrm[sl] > bv) {
+          bv = nrm[sl];
+          bi = rank + sl * CS;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_cval = bv;
+        s_cidx = bi;
+      }
+    }
+    cl.sync();
+    if (warp == 0) {  // the same pivot in every CTA
+      float bv = -1.f;
+      int bi = -1;
+      if (lane < CS) {
+        bv = *cl.map_shared_rank(&s_cval, lane);
+        bi = *cl.map_shared_rank(&s_cidx, lane);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_p = bi;
+        s_piv[j] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    const int owner = p < 0 ? -1 : p % CS;
+    if (owner == rank && warp == 0) {  // form reflector j from column p
+      float* x = col + (p / CS) * MR;
+      float s2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int a = lane + 32 * t;
+        if (a > j && a < nr) s2 = fmaf(x[a], x[a], s2);
+      }
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      const float alpha = x[j];
+      float tj = 0.f, beta = alpha, sc = 0.f;
+      if (s2 != 0.f) {
+        const float nr2 = sqrtf(alpha * alpha + s2);
+        beta = alpha >= 0.f ? -nr2 : nr2;
+        tj = (beta - alpha) / beta;
+        sc = 1.f / (alpha - beta);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int a = lane + 32 * t;
+        float v = 0.f;
+        if (a == j) v = 1.f;
+        else if (a > j && a < nr) {
+          v = x[a] * sc;
+          x[a] = v;
+        }
+        s_v[a] = v;
+        Vg[(long long)j * MR + a] = v;
+      }
+      if (lane == 0) {
+        x[j] = beta;
+        s_btau = tj;
+        nrm[p / CS] = -1.f;
+      }
+    }
+    cl.sync();
+    if (owner >= 0 && owner != rank) {
+      const float* rv = cl.map_shared_rank(s_v, owner);
+      for (int a = tid; a < MR; a += NT32) s_v[a] = rv[a];
+      if (tid == 0) s_tau[j] = *cl.map_shared_rank(&s_btau, owner);
+    } else if (tid == 0) {
+      s_tau[j] = s_btau;
+    }
+    __syncthreads();
+    const float tj = s_tau[j];
+    for (int sl = warp; sl < cpc; sl += nw) {
+      if (nrm[sl] < 0.f) continue;
+      float* y = col + sl * MR;
+      float d = 0.f;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int a = lane + 32 * t;
+        if (a >= j) d = fmaf(s_v[a], y[a], d);
+      }
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const float w = tj * d;
+      float s2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int a = lane + 32 * t;
+        if (a >= j) {
+          const float yn = fmaf(-w, s_v[a], y[a]);
+          y[a] = yn;
+          if (a > j && a < nr) s2 = fmaf(yn, yn, s2);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) nrm[sl] = s2;
+    }
+    __syncthreads();
+  }
+  // columns never chosen (nc > nr) follow in ascending order; inverse order
+  if (tid == 0) {  // a permutation whatever the norms were (non-finite input included)
+    for (int c = 0; c < nc; ++c) s_pos[c] = -1;
+    for (int q = 0; q < k1; ++q) {
+      const int c = s_piv[q];
+      if (c >= 0 && c < nc && s_pos[c] < 0) s_pos[c] = q;
+      else s_piv[q] = -1;
+    }
+    int nxt = 0;
+    for (int q = 0; q < nc; ++q)
+      if (q >= k1 || s_piv[q] < 0) {
+        while (nxt < nc && s_pos[nxt] >= 0) ++nxt;
+        if (nxt >= nc) break;
+        s_piv[q] = nxt;
+        s_pos[nxt] = q;
+      }
+    if (rank == 0 && k1_out) *k1_out = k1;
+  }
+  __syncthreads();
+  for (int sl = warp; sl < cpc; sl += nw) {
+    const int c = rank + sl * CS;
+    if (c >= nc) continue;
+    const int pos = s_pos[c];
+    if (pos < 0 || pos >= nc) continue;
+    for (int r = lane; r < k1; r += 32) R1[(long long)r * ldr1 + pos] = r <= pos ? (double)col[sl * MR + r] : 0.0;
+  }
+  __threadfence();
+  cl.sync();  // every reflector is in Vg and every CTA is done with its columns
+  // thin Q1: column q = H_0 ... H_{k1-1} e_q, for q = rank, rank + CS, ...
+  for (int sl = warp; sl < cpc; sl += nw) {
+    const int q = rank + sl * CS;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int a = lane + 32 * t;
+      col[sl * MR + a] = (a == q) ? 1.f : 0.f;
+    }
+  }
+  for (int j = k1 - 1; j >= 0; --j) {
+    __syncthreads();
+    for (int a = tid; a < MR; a += NT32) s_v[a] = __ldcg(Vg + (long long)j * MR + a);
+    __syncthreads();
+    const float tj = s_tau[j];
+    for (int sl = warp; sl < cpc; sl += nw) {
+      const int q = rank + sl * CS;
+      if (q >= k1 || q < j) continue;  // H_j leaves e_q alone for q < j
+      float* y = col + sl * MR;
+      float d = 0.f;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int a = lane + 32 * t;
+        if (a >= j) d = fmaf(s_v[a], y[a], d);
+      }
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const float w = tj * d;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int a = lane + 32 * t;
+        if (a >= j) y[a] = fmaf(-w, s_v[a], y[a]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int sl = warp; sl < cpc; sl += nw) {
+    const int q = rank + sl * CS;
+    if (q >= k1) continue;
+    for (int a = lane; a < nr; a += 32) Q1[(long long)a * ldq + q] = (double)col[sl * MR + a];
+  }
+}
+
 inline int eg(long long total) {
   long long g = (total + 255) / 256;
   return (int)std::max(1LL, std::min(g, 148LL * 8));
@@ -494,6 +728,32 @@ cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, D
   return cudaGetLastError();
 }
 
+static size_t qrcp_smem(int cpc) {
+  return ((size_t)cpc * 256 + cpc + 256 + 256) * sizeof(float) + 2 * (size_t)NT32 * sizeof(int);
+}
+
+cudaError_t qrcp_cluster(qtt_ctx* ctx, const double* Ain, long long lda, Dim nr, Dim nc, long long nmax, double* R1,
+                         long long ldr1, double* Q1, long long ldq, float* Vg, int* k1_out) {
+  if (nmax > 256) return cudaErrorInvalidValue;
+  // at most 16 columns per CTA (one per warp), at most 16 CTAs
+  const int CS = (int)std::min<long long>(16, std::max<long long>(1, (nmax + 15) / 16));
+  const int cpc = (int)((nmax + CS - 1) / CS);
+  if (cpc > 16) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(NT32);
+  cfg.stream = ctx->stream;
+  cfg.dynamicSmemBytes = qrcp_smem(cpc);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<256>, Ain, lda, nr, nc, cpc, R1, ldr1, Q1, ldq, Vg, k1_out);
+}
+
 cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st) {
   row_norms_kernel<<<(int)std::max(1LL, std::min(nmax, 148LL * 4)), 256, 0, st>>>(W, ldw, n, m, norms);
   return cudaGetLastError();
@@ -515,8 +775,15 @@ static cudaError_t init_jb() {
   return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+static cudaError_t init_qrcp() {
+  const void* k = (const void*)qrcp_cluster_kernel<256>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qrcp_smem(16));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 cudaError_t mixed_init() {
-  cudaError_t (*fs[])() = {init_jb<1, 1>, init_jb<2, 2>,init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
+  cudaError_t (*fs[])() = {init_qrcp, init_jb<1, 1>, init_jb<2, 2>,init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
                            init_j32<2, 1>, init_j32<2, 3>, init_j32<3, 2>, init_j32<3, 4>, init_j32<4, 3>,
                            init_j32<1, 3>, init_j32<1, 4>, init_j32<2, 4>, init_j32<3, 1>, init_j32<4, 1>,
                            init_j32<4, 2>};

@@ -65,6 +65,12 @@ cudaError_t ns_factor(const double* G, double* H, long long ld, Dim n, long long
 // rs: nmax doubles of scratch (row sums of |Omega|)
 cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, Dim n, long long nmax,
                          cudaStream_t st);
+// QR with column pivoting of A (nr x nc, A[a][i] = Ain[a*lda + i], nr and
+// nc <= nmax <= 256) in one cluster, FP32: R1 (k1 x nc) row-major (stride
+// ldr1), thin Q1 (nr x k1) row-major (stride ldq), k1 = min(nr, nc) to
+// *k1_out.  Vg: k1 * 256 floats of scratch.
+cudaError_t qrcp_cluster(qtt_ctx* ctx, const double* Ain, long long lda, Dim nr, Dim nc, long long nmax, double* R1,
+                         long long ldr1, double* Q1, long long ldq, float* Vg, int* k1_out);
 cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st);
 cudaError_t mixed_init();
 
