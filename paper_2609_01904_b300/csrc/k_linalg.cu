@@ -53,11 +53,11 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
 template <typename T>
 __device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
 
-template <typename T>
+template <typename T, int B>
 __device__ __forceinline__ void qr_form(T* x, long long j, long long m, T* tau, T* red) {
   const int tid = threadIdx.x;
   T s = T(0);
-  for (long long i = j + 1 + tid; i < m; i += NT) s = fma(x[i], x[i], s);
+  for (long long i = j + 1 + tid; i < m; i += B) s = fma(x[i], x[i], s);
   s = block_sum(s, red);
   const T alpha = x[j];
   T tj = T(0), beta = alpha;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void qr_form(T* x, long long j, long long m, T* tau, 
     beta = alpha >= T(0) ? -nrm : nrm;
     tj = (beta - alpha) / beta;
     const T sc = T(1) / (alpha - beta);
-    for (long long i = j + 1 + tid; i < m; i += NT) x[i] *= sc;
+    for (long long i = j + 1 + tid; i < m; i += B) x[i] *= sc;
   }
   __syncthreads();
   if (tid == 0) {
@@ -77,20 +77,20 @@ __device__ __forceinline__ void qr_form(T* x, long long j, long long m, T* tau, 
 
 // y <- (I - tau v v^T) y on rows j..m-1 (v_j = 1 implicit); v is another CTA's
 // column, read through L2
-template <typename T>
+template <typename T, int B>
 __device__ __forceinline__ void qr_apply(const T* v, T tj, T* y, long long j, long long m, T* red) {
   const int tid = threadIdx.x;
   T s = T(0);
-  for (long long i = j + 1 + tid; i < m; i += NT) s = fma(__ldcg(v + i), y[i], s);
+  for (long long i = j + 1 + tid; i < m; i += B) s = fma(__ldcg(v + i), y[i], s);
   s = block_sum(s, red);
   const T w = tj * (y[j] + s);
   if (tid == 0) y[j] -= w;
-  for (long long i = j + 1 + tid; i < m; i += NT) y[i] = fma(-w, __ldcg(v + i), y[i]);
+  for (long long i = j + 1 + tid; i < m; i += B) y[i] = fma(-w, __ldcg(v + i), y[i]);
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, Dim lda_d, T* W, long long ldw,
+template <typename T, int B>
+__global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, Dim lda_d, T* W, long long ldw,
                                                 Dim m_d, Dim n_d, T* tau, double* Rout, int r_rowmajor,
                                                 long long ldr, double* Qout, int* kq_out, int* flag,
                                                 DevSync* sync) {
@@ -103,12 +103,12 @@ __global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
 
   for (long long c = b; c < n; c += G)
-    for (long long i = tid; i < m; i += NT) W[c * ldw + i] = T(Ain[c * lda + i]);
-  for (long long j = (long long)b * NT + tid; j < kq; j += (long long)G * NT) flag[j] = 0;
+    for (long long i = tid; i < m; i += B) W[c * ldw + i] = T(Ain[c * lda + i]);
+  for (long long j = (long long)b * B + tid; j < kq; j += (long long)G * B) flag[j] = 0;
   if (!grid_sync(sync)) return;
 
   if (kq > 0 && b == 0) {  // column 0 is owned by CTA 0
-    qr_form(W, 0, m, tau, red);
+    qr_form<T, B>(W, 0, m, tau, red);
     if (tid == 0) {
       __threadfence();
       st_release(flag + 0, 1);
@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, 
     const long long nx = j + 1;
     if (nx < n && nx % G == b) {
       T* y = W + nx * ldw;
-      if (tj != T(0)) qr_apply(v, tj, y, j, m, red);
+      if (tj != T(0)) qr_apply<T, B>(v, tj, y, j, m, red);
       if (nx < kq) {
-        qr_form(y, nx, m, tau, red);
+        qr_form<T, B>(y, nx, m, tau, red);
         if (tid == 0) {
           __threadfence();
           st_release(flag + nx, 1);
@@ -138,14 +138,14 @@ __global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, 
     if (tj != T(0)) {
       long long c0 = b + ((j + 2 - b + G - 1) / G) * G;  // first owned column > j+1
       if (j + 2 <= b) c0 = b;
-      for (long long c = c0; c < n; c += G) qr_apply(v, tj, W + c * ldw, j, m, red);
+      for (long long c = c0; c < n; c += G) qr_apply<T, B>(v, tj, W + c * ldw, j, m, red);
     }
   }
   __syncthreads();
 
   // R: rows 0..kq-1 of the owned columns
   for (long long c = b; c < n; c += G) {
-    for (long long i = tid; i < kq; i += NT) {
+    for (long long i = tid; i < kq; i += B) {
       const double r = i <= c ? (double)W[c * ldw + i] : 0.0;
       if (r_rowmajor) Rout[i * ldr + c] = r;
       else Rout[c * ldr + i] = r;
@@ -159,21 +159,21 @@ __global__ void __launch_bounds__(NT) qr_kernel(const double* __restrict__ Ain, 
   __syncthreads();
   if (!s_ok) return;
   for (long long c = b; c < kq; c += G) {
-    for (long long i = tid; i < m; i += NT) ysh[i] = (i == c) ? T(1) : T(0);
+    for (long long i = tid; i < m; i += B) ysh[i] = (i == c) ? T(1) : T(0);
     __syncthreads();
     for (long long i = c; i >= 0; --i) {
       const T ti = __ldcg(tau + i);
       if (ti == T(0)) continue;
       const T* v = W + i * ldw;
       T s = T(0);
-      for (long long l = i + 1 + tid; l < m; l += NT) s = fma(__ldcg(v + l), ysh[l], s);
+      for (long long l = i + 1 + tid; l < m; l += B) s = fma(__ldcg(v + l), ysh[l], s);
       s = block_sum(s, red);
       const T w = ti * (ysh[i] + s);
       if (tid == 0) ysh[i] -= w;
-      for (long long l = i + 1 + tid; l < m; l += NT) ysh[l] = fma(-w, __ldcg(v + l), ysh[l]);
+      for (long long l = i + 1 + tid; l < m; l += B) ysh[l] = fma(-w, __ldcg(v + l), ysh[l]);
       __syncthreads();
     }
-    for (long long i = tid; i < m; i += NT) Qout[i * kq + c] = (double)ysh[i];
+    for (long long i = tid; i < m; i += B) Qout[i * kq + c] = (double)ysh[i];
     __syncthreads();
   }
 }
@@ -430,7 +430,10 @@ static cudaError_t qr_launch(qtt_ctx* ctx, const double* Ain, Dim lda, double* W
   void* args[] = {(void*)&Ain, (void*)&lda, (void*)&W, (void*)&ldw, (void*)&m, (void*)&n, (void*)&tau,
                   (void*)&Rout, (void*)&rrm, (void*)&ldr, (void*)&Qout, (void*)&kq_out, (void*)&flag,
                   (void*)&sync};
-  return coop_launch((const void*)qr_kernel<T>, grid, NT, args, smem, ctx->stream);
+  // long columns (ldw bounds the rows): 1024 threads shorten each pass over a
+  // column, which the reflector chain waits on
+  if (ldw >= 2048) return coop_launch((const void*)qr_kernel<T, 1024>, grid, 1024, args, smem, ctx->stream);
+  return coop_launch((const void*)qr_kernel<T, NT>, grid, NT, args, smem, ctx->stream);
 }
 
 cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
@@ -476,18 +479,19 @@ int* jacobi_log_slot(qtt_ctx* ctx) {
 }
 
 cudaError_t linalg_init(int device) {
-  cudaError_t e = cudaFuncSetAttribute((const void*)qr_kernel<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute((const void*)qr_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
+  const void* ks[] = {(const void*)qr_kernel<double, NT>, (const void*)qr_kernel<float, NT>,
+                      (const void*)qr_kernel<double, 1024>, (const void*)qr_kernel<float, 1024>};
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
 int coop_max_blocks(int num_sms) {
   int a = 0, b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)jacobi_kernel, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)qr_kernel<double>, NT, 200 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)qr_kernel<double, NT>, NT, 200 * 1024);
   int per = std::min(std::max(a, 1), std::max(b, 1));
   (void)per;
   // one CTA per SM: the FP64 pipe is per SM, more CTAs only add barrier traffic
