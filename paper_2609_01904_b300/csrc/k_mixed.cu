@@ -11,7 +11,7 @@
 // Schulz re-orthonormalisation J <- J (3I - J^T J)/2, W = R J, G = W^T W, a
 // simultaneous first-order Jacobi correction J <- J (I + Omega) with
 // Omega_ij = G_ij / (G_jj - G_ii) (damped inside clusters of near-equal
-// values), three times, then sigma_i = |W e_i| in FP64.  The rotation is
+// values), twice, then sigma_i = |W e_i| in FP64.  The rotation is
 // orthogonal to FP64 rounding; the contamination of every vector by the
 // directions of much larger values (FP32 rounding of the first stage) is
 // removed, so well separated values come out to FP64 accuracy, while values
@@ -643,7 +643,7 @@ template <int EA, int EJ>
 static cudaError_t launch_j32(cudaLaunchConfig_t* cfg, const double* V, long long ldv, Dim nv, Dim m, double* J,
                               long long ldj, int cpc, int* log) {
   // FP32 stops an order of magnitude above its rounding floor; the FP64
-  // refinement squares the remaining non-orthogonality three times
+  // refinement squares the remaining non-orthogonality twice
   const int max_sweeps = 20;
   const float tol = 1e-4f, tol_abs = 1e-6f;
   return cudaLaunchKernelEx(cfg, jacobi32_cluster_kernel<EA, EJ>, V, ldv, nv, m, J, ldj, cpc, max_sweeps, tol, tol_abs,

@@ -393,7 +393,7 @@ GemmArgs gram(const double* X, long long ldx, double* G, long long ldg, Dim rows
 
 // One-sided Jacobi of nv vectors V (length m) in the step's precision.  The
 // mixed form: FP32 Jacobi in one cluster, then FP64 refinement (Newton-Schulz
-// and three damped first-order corrections from the Gram of W = J V, two
+// and two damped first-order corrections from the Gram of W = J V, two
 // final Newton-Schulz steps), sigma = |W_c|.
 qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, long long mmax,
                       double* J, long long ldj, double* norms) {
@@ -413,7 +413,7 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
                          ctx->stream));
     return QTT_OK;
   };
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < 2; ++it) {
     CKS(ns());
     KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
     KL(KC_REFINE, gemm_f64(gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
@@ -484,7 +484,6 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     g.sci = dconst(ldv);
     g.scj = dconst(1);
     KL(KC_REFINE, gemm_f64(g, nvmax, nvmax, 1, 1, ctx->stream));
-    CKS(ns_rows(ctx, s.d_jh, ldv, dptr(k1), nv, nvmax, nvmax));
     CKS(ns_rows(ctx, s.d_jh, ldv, dptr(k1), nv, nvmax, nvmax));
     KL(KC_POST, svd_post(ctx, s.d_norm, dptr(k1), dptr(kq), nv, s.d_jh, ldv, eps, chi, rank_cap, rank_out, sig,
                          disc_out, Jp, Jt, nsv_out));
