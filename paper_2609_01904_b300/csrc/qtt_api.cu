@@ -467,7 +467,7 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     // orthogonal factors, re-orthonormalised in FP64.
     int* k1 = s.d_ints + 1;
     KL(KC_QR, qr_any(ctx, Tv, ell, s.d_tq, ellmax, ell, nv, nvmax, s.d_rv, false, nullptr, kq, ldv, 0));
-    KL(KC_QR, qrcp_cluster(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, s.d_tt, ldv, s.d_qt, ldv,
+    KL(KC_QRCP, qrcp_cluster(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, s.d_tt, ldv, s.d_qt, ldv,
                            reinterpret_cast<float*>(s.d_tq), k1));
     CKS(jacobi_any(ctx, s.d_tt, ldv, dptr(k1), dptr(kq), nvmax, nvmax, s.d_jv, ldv, s.d_norm));
     GemmArgs g = gemm0();  // J_M[c][a] = sum_k J[c][k] Q1[a][k]

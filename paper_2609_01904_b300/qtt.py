@@ -47,8 +47,9 @@ _PI = ctypes.POINTER(ctypes.c_int)
 _PD = ctypes.POINTER(ctypes.c_double)
 _PL = ctypes.POINTER(ctypes.c_long)
 
-QTT_KCLASSES = 10
-KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "copy", "fdtd", "refine", "other"]
+QTT_KCLASSES = 11
+KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "copy", "fdtd", "refine", "other",
+                  "qrcp"]
 
 
 class qtt_profile(ctypes.Structure):
