@@ -162,6 +162,18 @@ qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, doubl
 qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2,
                     qtt_mps* psi_prev, qtt_mps* psi_cur, const long* src_ixiz, double src_amp);
 
+/* The same step as qtt_step, replayed from a CUDA graph: the first call
+ * for a given (L, c2, lambda2, source position, pair of state buffers)
+ * captures the step's launches twice (once for each role of the two state
+ * buffers, which exchange roles every step) on the context stream; later
+ * calls write the source sample to the device and launch the matching graph,
+ * one launch instead of ~2000.  Any other argument, or a workspace that had
+ * to grow, makes it capture again.  Not for contexts with use_learned_rank
+ * (the learned rounding synchronises with the host) nor while per-kernel
+ * timing is on (QTT_EINVAL).  Results are those of qtt_step. */
+qtt_status qtt_step_graph(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* psi_prev,
+                          qtt_mps* psi_cur, const long* src_ixiz, double src_amp);
+
 /* Batched shots.  A batch holds one context per shot (each with its own
  * chi_max and workspace, all on `cuda_stream`) and a pool of min(nshots, 8)
  * internal streams; qtt_step_batched advances every shot by one step
@@ -185,6 +197,9 @@ qtt_ctx* qtt_batch_ctx(qtt_batch* batch, int shot);
 qtt_status qtt_step_batched(qtt_batch* batch, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps** prev,
                             qtt_mps** cur, const long* src_ixiz, const double* src_amp);
 void qtt_batch_destroy(qtt_batch* batch);
+/* on != 0: qtt_step_batched steps every shot through qtt_step_graph (one
+ * graph launch per shot and step instead of ~2000 kernel launches). */
+qtt_status qtt_batch_set_graphs(qtt_batch* batch, int on);
 
 /* ------------------------------------------------------------ learned form
  * The rounding rule of Sec. 4.3 stays the judge; a learned model only

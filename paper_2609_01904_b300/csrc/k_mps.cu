@@ -97,7 +97,7 @@ __global__ void mps_sum_kernel(SumArgs a) {
         if (k == 0) v *= a.coef[t];
       } else {  // rank-1 source: one-hot on the source's bits
         v = (s == a.src_bits[k]) ? 1.0 : 0.0;
-        if (k == 0) v *= a.src_amp;
+        if (k == 0) v *= a.src_amp_dev ? *a.src_amp_dev : a.src_amp;
       }
     }
     out[e] = v;

@@ -19,6 +19,7 @@ struct SumArgs {
   int has_src;
   int src_bits[kMaxSites];
   double src_amp;
+  const double* src_amp_dev;  // when set, the amplitude is read from here (graph replays)
 };
 
 struct SampleArgs {

@@ -180,6 +180,11 @@ void ws_free(qtt_ctx* ctx) {
     }
   s.phi = s.eta = s.theta = s.spare = nullptr;
   ctx->ws_ready = false;
+  for (auto& g : ctx->gexec)  // graphs point into the workspace
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
 }
 
 struct Sizes {
@@ -698,6 +703,7 @@ qtt_status form_sum(qtt_ctx* ctx, const std::vector<std::pair<double, const Mps*
   a.out_ranks = out->ranks;
   a.has_src = src ? 1 : 0;
   a.src_amp = amp;
+  a.src_amp_dev = ctx->capturing ? ctx->d_amp : nullptr;
   if (src) {
     const int n = ctx->p.n;
     for (int k = 0; k < d; ++k) {
@@ -1060,6 +1066,8 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
     cudaEventDestroy(e.second);
   }
   if (ctx->prof.d_log) cudaFree(ctx->prof.d_log);
+  if (ctx->d_amp) cudaFree(ctx->d_amp);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   delete ctx;
 }
 
@@ -1283,8 +1291,29 @@ qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, doubl
   return QTT_OK;
 }
 
-qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* prev, qtt_mps* cur,
-                    const long* src, double amp) {
+}  // extern "C"
+
+namespace {
+
+// The launches of one step (Eq. 17): zip-up of L, zip-up of diag(c^2), the
+// sum with the source, the round into prev.  No host synchronisation.
+qtt_status step_body(qtt_ctx* ctx, const Mpo* L, const Mps* c2, const std::vector<int>& rc, const Caps& c,
+                     double lambda2, Mps* prev, Mps* cur, const long* src, double amp) {
+  Workspace& s = ctx->ws;
+  struct MpScope {  // the reduced-precision form applies inside the step only
+    qtt_ctx* c;
+    explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec == QTT_FP32); }
+    ~MpScope() { c->use_mp = false; }
+  } mp_scope(ctx);
+  CKS(zipup_L(ctx, L, cur, s.phi, c));
+  CKS(zipup_C(ctx, c2, rc, s.phi, s.eta, c));
+  CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta));
+  CKS(tt_round(ctx, s.theta, prev));
+  return QTT_OK;
+}
+
+qtt_status step_checks(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* prev,
+                       qtt_mps* cur, const long* src) {
   if (!ctx || !L || !c2 || !prev || !cur) return fail(QTT_EINVAL, "null argument");
   if (L->d != ctx->d || c2->d != ctx->d || prev->d != ctx->d || cur->d != ctx->d)
     return fail(QTT_EINVAL, "handle from another grid size");
@@ -1293,6 +1322,94 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
   const long N = 1L << ctx->p.n;
   if (src && (src[0] < 0 || src[0] >= N || src[1] < 0 || src[1] >= N))
     return fail(QTT_EINVAL, "source outside the grid");
+  return QTT_OK;
+}
+
+void swap_roles(Mps* a, Mps* b) {
+  std::swap(a->data, b->data);
+  std::swap(a->ranks, b->ranks);
+}
+
+void drop_graphs(qtt_ctx* ctx) {
+  for (auto& e : ctx->gexec)
+    if (e) {
+      cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+qtt_status qtt_step_graph(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* prev,
+                          qtt_mps* cur, const long* src, double amp) {
+  CKS(step_checks(ctx, L, c2, lambda2, prev, cur, src));
+  if (ctx->p.use_learned_rank) return fail(QTT_EINVAL, "the learned rounding synchronises with the host: use qtt_step");
+  if (ctx->prof.timing) return fail(QTT_EINVAL, "per-kernel timing is on: use qtt_step");
+  std::vector<int> rc = c2->cap;
+  if (c2->host_ranks.size() == (size_t)ctx->d + 1) rc = c2->host_ranks;
+  CKS(ensure_ws(ctx, L->w, rc));
+  Caps c = step_caps(ctx, L->w, rc);
+  if (!ctx->d_amp) CK(cudaMalloc(&ctx->d_amp, sizeof(double)));
+  const long sk[3] = {src ? 1L : 0L, src ? src[0] : 0L, src ? src[1] : 0L};
+  auto same = [&](int g) {
+    return ctx->gexec[g] && ctx->gkey[g][0] == L && ctx->gkey[g][1] == c2 && ctx->gkey[g][2] == prev->data &&
+           ctx->gkey[g][3] == cur->data && ctx->gkey_lam == lambda2 && ctx->gkey_src[0] == sk[0] &&
+           ctx->gkey_src[1] == sk[1] && ctx->gkey_src[2] == sk[2];
+  };
+  int g = same(0) ? 0 : (same(1) ? 1 : -1);
+  if (g < 0) {  // capture the step for both roles of the pair of state buffers
+    drop_graphs(ctx);
+    if (!ctx->gstream) CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    long long before[KC_N];
+    for (int r = 0; r < 2; ++r) {
+      for (int k = 0; k < KC_N; ++k) before[k] = ctx->prof.launches[k];
+      // capture on the context's own capture stream: recording runs nothing,
+      // and the replays go to the caller's stream
+      CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+      const cudaStream_t user = ctx->stream;
+      ctx->stream = ctx->gstream;
+      ctx->capturing = true;
+      const qtt_status st = step_body(ctx, L, c2, rc, c, lambda2, prev, cur, src, amp);
+      ctx->capturing = false;
+      ctx->stream = user;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(ctx->gstream, &graph);
+      cudaError_t ei = cudaErrorUnknown;
+      if (st == QTT_OK && e == cudaSuccess) ei = cudaGraphInstantiate(&ctx->gexec[r], graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      for (int k = 0; k < KC_N; ++k) {
+        ctx->glaunches[k] = ctx->prof.launches[k] - before[k];
+        ctx->prof.launches[k] = before[k];
+      }
+      if (st != QTT_OK || e != cudaSuccess || ei != cudaSuccess) {
+        if (r == 1) swap_roles(prev, cur);
+        ctx->gexec[r] = nullptr;
+        drop_graphs(ctx);
+        if (st != QTT_OK) return st;
+        return fail(QTT_ECUDA, std::string("step capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ei));
+      }
+      ctx->gkey[r][0] = L;
+      ctx->gkey[r][1] = c2;
+      ctx->gkey[r][2] = prev->data;
+      ctx->gkey[r][3] = cur->data;
+      swap_roles(prev, cur);  // the second graph serves the exchanged roles
+    }
+    ctx->gkey_lam = lambda2;
+    for (int k = 0; k < 3; ++k) ctx->gkey_src[k] = sk[k];
+    g = 0;
+  }
+  CK(cudaMemcpyAsync(ctx->d_amp, &amp, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaGraphLaunch(ctx->gexec[g], ctx->stream));
+  for (int k = 0; k < KC_N; ++k) ctx->prof.launches[k] += ctx->glaunches[k];
+  swap_roles(prev, cur);
+  return QTT_OK;
+}
+
+qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* prev, qtt_mps* cur,
+                    const long* src, double amp) {
+  CKS(step_checks(ctx, L, c2, lambda2, prev, cur, src));
   std::vector<int> rc = c2->cap;  // c^2 ranks are fixed; capacities bound them
   if (c2->host_ranks.size() == (size_t)ctx->d + 1) rc = c2->host_ranks;
   CKS(ensure_ws(ctx, L->w, rc));
@@ -1305,15 +1422,7 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
     ctx->pending_prop.clear();
     ctx->have_prop = true;
   }
-  struct MpScope {  // the reduced-precision form applies inside the step only
-    qtt_ctx* c;
-    explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec == QTT_FP32); }
-    ~MpScope() { c->use_mp = false; }
-  } mp_scope(ctx);
-  CKS(zipup_L(ctx, L, cur, s.phi, c));
-  CKS(zipup_C(ctx, c2, rc, s.phi, s.eta, c));
-  CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta));
-  CKS(tt_round(ctx, s.theta, prev));
+  CKS(step_body(ctx, L, c2, rc, c, lambda2, prev, cur, src, amp));
   ctx->have_prop = false;  // proposals are for one step
   if (ctx->p.use_learned_rank && ctx->mlp) CKS(propose_ranks(ctx, prev));
   // prev now holds u^{k+1}: exchange buffers so that prev = u^k, cur = u^{k+1}
@@ -1467,6 +1576,7 @@ struct qtt_batch {
   std::vector<cudaEvent_t> done;
   cudaEvent_t start = nullptr;
   cudaStream_t user = nullptr;
+  bool graphs = false;  // shots step through qtt_step_graph
 };
 
 extern "C" {
@@ -1520,6 +1630,12 @@ qtt_status qtt_batch_create(const qtt_params* base, int nshots, const int* chi_p
   return QTT_OK;
 }
 
+qtt_status qtt_batch_set_graphs(qtt_batch* b, int on) {
+  if (!b) return fail(QTT_EINVAL, "null batch");
+  b->graphs = on != 0;
+  return QTT_OK;
+}
+
 qtt_ctx* qtt_batch_ctx(qtt_batch* b, int shot) {
   if (!b || shot < 0 || shot >= (int)b->ctx.size()) return nullptr;
   return b->ctx[shot];
@@ -1542,8 +1658,8 @@ qtt_status qtt_step_batched(qtt_batch* b, const qtt_mpo* L, const qtt_mps* c2, d
   std::vector<std::string> msg(S);
   auto worker = [&](int s) {
     for (int i = s; i < n; i += S) {
-      qtt_status r = qtt_step(b->ctx[i], L, c2, lambda2, prev[i], cur[i], src ? src + 2 * i : nullptr,
-                              src ? amp[i] : 0.0);
+      qtt_status r = (b->graphs ? qtt_step_graph : qtt_step)(b->ctx[i], L, c2, lambda2, prev[i], cur[i],
+                                                             src ? src + 2 * i : nullptr, src ? amp[i] : 0.0);
       if (r != QTT_OK) {
         st[s] = r;
         msg[s] = g_err;

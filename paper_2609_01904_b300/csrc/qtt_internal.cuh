@@ -263,6 +263,16 @@ struct qtt_ctx {
   bool have_prop = false;          // d_prop holds proposals from the previous step
   std::vector<int> pending_prop;   // proposals set by the caller for the next step
   long long rf_attempts = 0, rf_accepts = 0;
+  // CUDA-graph form of the step: two graphs (the two roles of the pair of
+  // state buffers), their keys, the launches one replay makes per class
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  const void* gkey[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+  double gkey_lam = 0.0;
+  long gkey_src[3] = {0, 0, 0};
+  long long glaunches[16] = {0};
+  double* d_amp = nullptr;  // source sample of the step being replayed
+  cudaStream_t gstream = nullptr;  // capture stream (the legacy stream cannot be captured)
+  bool capturing = false;   // inside a capture: the sum reads d_amp
 };
 
 namespace qtt {

@@ -80,6 +80,8 @@ _SIGS = {
     "qtt_batch_create": [ctypes.POINTER(qtt_params), _I, _PI, _P, ctypes.POINTER(_P)],
     "qtt_step_batched": [_P, _P, _P, _D, ctypes.POINTER(_P), ctypes.POINTER(_P), _PL, _PD],
     "qtt_profile_read": [_P, ctypes.POINTER(qtt_profile)],
+    "qtt_step_graph": [_P, _P, _P, _D, _P, _P, _PL, _D],
+    "qtt_batch_set_graphs": [_P, _I],
     "qtt_mps_save": [_P, _P, ctypes.c_char_p],
     "qtt_mps_load": [_P, ctypes.c_char_p, ctypes.POINTER(_P)],
     "qtt_mlp_create": [ctypes.POINTER(ctypes.c_float), _I, _P, ctypes.POINTER(_P)],
@@ -300,6 +302,14 @@ def qtt_inject_source(psi: Mps, ix: int, iz: int, amp: float) -> None:
     _check(_lib.qtt_inject_source(psi.ctx.h, psi.h, ix, iz, amp), "qtt_inject_source")
 
 
+def qtt_step_graph(L: Mpo, c2: Mps, lambda2: float, psi_prev: Mps, psi_cur: Mps, src=None, amp: float = 0.0) -> None:
+    """qtt_step replayed from a CUDA graph captured on the first call."""
+    s = None
+    if src is not None:
+        s = (ctypes.c_long * 2)(int(src[0]), int(src[1]))
+    _check(_lib.qtt_step_graph(psi_cur.ctx.h, L.h, c2.h, lambda2, psi_prev.h, psi_cur.h, s, amp), "qtt_step_graph")
+
+
 def qtt_step(L: Mpo, c2: Mps, lambda2: float, psi_prev: Mps, psi_cur: Mps, src=None, amp: float = 0.0) -> None:
     """Eq. 17: on return psi_prev holds u^k and psi_cur holds u^{k+1}."""
     s = None
@@ -416,6 +426,10 @@ def qtt_batch_destroy(batch: Batch) -> None:
     """Drops the Python references; the C batch goes with the last state."""
     batch.ctxs = []
     batch.hold = None
+
+
+def qtt_batch_set_graphs(batch: Batch, on: bool = True) -> None:
+    _check(_lib.qtt_batch_set_graphs(batch.h, int(on)), "qtt_batch_set_graphs")
 
 
 def qtt_step_batched(batch: Batch, L: Mpo, c2: Mps, lambda2: float, prev: list, cur: list, src=None,

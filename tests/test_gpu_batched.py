@@ -138,3 +138,26 @@ def test_batched_step_rejects_a_state_of_another_shot(q):
     with pytest.raises(q.QttError) as e:
         q.qtt_step_batched(batch, L, C, 1e-8, prev, cur)
     assert e.value.status == q.QTT_EINVAL
+
+
+def test_batched_graph_replays_equal_batched_steps(q):
+    """The same batch stepped through graph replays (qtt_batch_set_graphs)
+    reproduces the plainly launched batch bit for bit."""
+    n, N, eps = 5, 32, 1e-9
+    chis = [16, 8, 32, 16, 8]
+    c = W.layered_model(n, 40.0, 3)
+    lam2 = (0.5 / c.max()) ** 2
+    srcs = [(3 + 5 * s, 2 + s) for s in range(len(chis))]
+    out = []
+    for graphs in (False, True):
+        batch = q.qtt_batch_create(n, len(chis), chis, chi_max=32, eps=eps, chi_c=12, eps_c=1e-8, prec="fp32")
+        q.qtt_batch_set_graphs(batch, graphs)
+        L = q.qtt_laplacian_mpo(batch.ctxs[0])
+        C = q.qtt_velocity_mps(batch.ctxs[0], _t(c))
+        prev = [q.qtt_mps_create_zero(x) for x in batch.ctxs]
+        cur = [q.qtt_mps_create_zero(x) for x in batch.ctxs]
+        for k in range(12):
+            q.qtt_step_batched(batch, L, C, lam2, prev, cur, srcs, [np.sin(0.5 * k + s) for s in range(len(chis))])
+        out.append([_dense(q, x, N) for x in cur])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
