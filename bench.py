@@ -335,6 +335,7 @@ def run_shots(args):
     t0 = time.time()
     batch = q.qtt_batch_create(wl.n, ns, chis, order=wl.order, bc=wl.bc, chi_max=max(chis), eps=wl.eps,
                                chi_c=wl.chi_c, eps_c=wl.eps_c, prec=args.form, stream=stream)
+    q.qtt_batch_set_graphs(batch, bool(args.graph))
     N = wl.N
     with torch.cuda.stream(stream):
         c_dev = torch.as_tensor(c, device="cuda")
@@ -384,7 +385,8 @@ def run_shots(args):
         flush.fill_(-1.0)
         e0.record(stream)
         for s in range(ns):
-            q.qtt_step(L, C, lam2, prev[s], cur[s], wl.sources[s], float(amps[k]))
+            (q.qtt_step_graph if args.graph else q.qtt_step)(L, C, lam2, prev[s], cur[s], wl.sources[s],
+                                                             float(amps[k]))
         e1.record(stream)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
@@ -394,6 +396,7 @@ def run_shots(args):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.form == "fp64" else "f32+f64", "data": "synthetic (seeded layered section)",
         "config": {"workload": wl.name, "n": wl.n, "shots": ns, "chi_per_shot": chis, "eps": wl.eps,
+                   "graph": bool(args.graph),
                    "form": args.form, "state": f"mid-run (step {SHOTS_MID_RUN})", "max_rank_start": ranks0,
                    "l2": "flushed between timed steps (256 MiB write)", "setup_s": round(setup_s, 1)},
         "gpu_launches": int(launches),
