@@ -419,7 +419,8 @@ __global__ void __launch_bounds__(NT32) qrcp_cluster_kernel(const double* __rest
   float* col = smf;                              // cpc columns of MR floats
   float* nrm = col + (long long)cpc * MR;        // remaining squared norms (-1: chosen)
   float* s_v = nrm + cpc;                        // reflector of the current step
-  float* s_tau = s_v + MR;                       // tau of every step
+  float* s_v2 = s_v + MR;                        // second reflector buffer (forming Q1)
+  float* s_tau = s_v2 + MR;                      // tau of every step
   int* s_piv = reinterpret_cast<int*>(s_tau + MR);  // logical -> physical column (<= NT32 columns)
   int* s_pos = s_piv + NT32;                     // physical -> logical
   __shared__ float s_cval, s_btau;
@@ -598,10 +599,15 @@ __global__ void __launch_bounds__(NT32) qrcp_cluster_kernel(const double* __rest
       col[sl * MR + a] = (a == q) ? 1.f : 0.f;
     }
   }
+  // reflectors come from L2 one step ahead (a register per thread) into two
+  // alternating shared buffers: one CTA barrier per reflector
+  static_assert(MR <= NT32, "one reflector element per thread");
+  float nxt = (tid < MR && k1 > 0) ? __ldcg(Vg + (long long)(k1 - 1) * MR + tid) : 0.f;
   for (int j = k1 - 1; j >= 0; --j) {
+    float* vb = (j & 1) ? s_v2 : s_v;
+    if (tid < MR) vb[tid] = nxt;
     __syncthreads();
-    for (int a = tid; a < MR; a += NT32) s_v[a] = __ldcg(Vg + (long long)j * MR + a);
-    __syncthreads();
+    if (j > 0 && tid < MR) nxt = __ldcg(Vg + (long long)(j - 1) * MR + tid);
     const float tj = s_tau[j];
     for (int sl = warp; sl < cpc; sl += nw) {
       const int q = rank + sl * CS;
@@ -611,14 +617,14 @@ __global__ void __launch_bounds__(NT32) qrcp_cluster_kernel(const double* __rest
 #pragma unroll
       for (int t = 0; t < PER; ++t) {
         const int a = lane + 32 * t;
-        if (a >= j) d = fmaf(s_v[a], y[a], d);
+        if (a >= j) d = fmaf(vb[a], y[a], d);
       }
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       const float w = tj * d;
 #pragma unroll
       for (int t = 0; t < PER; ++t) {
         const int a = lane + 32 * t;
-        if (a >= j) y[a] = fmaf(-w, s_v[a], y[a]);
+        if (a >= j) y[a] = fmaf(-w, vb[a], y[a]);
       }
     }
   }
@@ -729,7 +735,7 @@ cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, D
 }
 
 static size_t qrcp_smem(int cpc) {
-  return ((size_t)cpc * 256 + cpc + 256 + 256) * sizeof(float) + 2 * (size_t)NT32 * sizeof(int);
+  return ((size_t)cpc * 256 + cpc + 3 * 256) * sizeof(float) + 2 * (size_t)NT32 * sizeof(int);
 }
 
 cudaError_t qrcp_cluster(qtt_ctx* ctx, const double* Ain, long long lda, Dim nr, Dim nc, long long nmax, double* R1,

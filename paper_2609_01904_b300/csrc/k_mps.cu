@@ -240,7 +240,7 @@ __global__ void fdtd_kernel(const double* __restrict__ c2, double lambda2, const
   const long long N = 1LL << n, total = N * N;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long x = idx / N, z = idx % N;
+    const long long x = idx >> n, z = idx & (N - 1);  // N = 2^n
     const double c = uc[idx];
     double nb;
     if (bc == QTT_BC_PERIODIC) {
