@@ -12,7 +12,7 @@ are saturated at chi_max; per-step cost depends only on the ranks.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (the
-stepper does not shard, see DESIGN.md): value = N * steps / max-rank time.
+stepper does not shard): value = N * steps / max-rank time.
 """
 from __future__ import annotations
 
@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -53,7 +54,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"qtt_bench_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

@@ -202,7 +202,7 @@ void qtt_batch_destroy(qtt_batch* batch);
 qtt_status qtt_batch_set_graphs(qtt_batch* batch, int on);
 
 /* ------------------------------------------------------------ learned form
- * The rounding rule of Sec. 4.3 stays the judge; a learned model only
+ * The rounding rule of Sec. 4.3 still decides every truncation; a learned model only
  * proposes, per bond, the rank of the next step's round, whose SVD then first
  * tries a randomised range finder of width proposal + oversample (Halko,
  * Martinsson & Tropp 2011, Algorithm 4.1 with the direct SVD of Sec. 5.1):

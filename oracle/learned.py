@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY, like ``qtt_oracle``: only ``tests/``,
 legs of ``bench.py`` may use it.  It shares no code with the CUDA library.
 
 The paper rounds every bond with a full SVD (Sec. 4.3).  The learned form
-keeps that rule as the judge and only changes how the kept subspace is found:
+keeps that rule as the arbiter and only changes how the kept subspace is found:
 
 * a small MLP (3 linear layers, width 128, ReLU, FP32 parameters) reads 40
   features of a bond's singular-value spectrum at step k and proposes the

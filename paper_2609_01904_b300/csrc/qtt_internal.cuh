@@ -254,7 +254,7 @@ struct qtt_ctx {
   bool use_mp = false;      // inside a reduced-precision step: FP32 contractions and QR, mixed SVD
   long long ws_nvmax = 0;   // widest SVD (vectors) the workspace holds
   long long ws_ellmax = 0;  // longest vector of a step SVD
-  // learned form (Sec. 4.3 rule kept as the judge)
+  // learned form (the Sec. 4.3 rule still decides every truncation)
   qtt_mlp* mlp = nullptr;          // rank model (not owned)
   const double* sketch = nullptr;  // Gaussian test matrix, row-major rows x cols (not owned)
   long long sketch_rows = 0, sketch_cols = 0;
