@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
   int sweep = 0;
   for (sweep = 0; sweep < max_sweeps && nv >= 2; ++sweep) {
     if (tid == 0) s_cnt = 0;
+    int rot = 0;  // this thread's warp rotated a pair in this sweep
     cl.sync();
     for (int t = 0; t < NB - 1; ++t) {
       // this CTA's block pair in block round t (circle method over NB blocks)
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
               uj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
                                               sn * p.w + cs * r.w);
             }
-            if (lane == 0) atomicAdd(&s_cnt, 1);
+            rot = 1;
           }
         }
         __syncthreads();
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
         for (int e = tid; e < B * MST / 4; e += NT32) dA[e] = sA[e];
         for (int e = tid; e < B * JST / 4; e += NT32) dJ[e] = sJ[e];
       }
+      if (t == NB - 2 && rot) s_cnt = 1;  // a flag, not a count: only zero matters
       cl.sync();
     }
     int total = 0;
