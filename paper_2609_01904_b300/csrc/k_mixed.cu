@@ -203,16 +203,32 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
         if (bq < 0) bq += NB - 1;
       }
       const int blk[2] = {bp, bq};
-      // copy in (float4 through distributed shared memory)
-      for (int h = 0; h < 2; ++h) {
-        const float4* srcA = reinterpret_cast<const float4*>(
-            cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
-        const float4* srcJ = reinterpret_cast<const float4*>(
-            cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
-        float4* dA = reinterpret_cast<float4*>(wA + h * B * MST);
-        float4* dJ = reinterpret_cast<float4*>(wJ + h * B * JST);
-        for (int e = tid; e < B * MST / 4; e += NT32) dA[e] = srcA[e];
-        for (int e = tid; e < B * JST / 4; e += NT32) dJ[e] = srcJ[e];
+      // copy in (float4 through distributed shared memory): every thread
+      // issues all its remote loads before its first store, so the copy
+      // costs one round trip, not one per element
+      static_assert(B * MST / 4 == NT32 * EA && B * JST / 4 == NT32 * EJ, "one float4 per thread and unit");
+      {
+        float4 ra[2][EA], rj[2][EJ];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4* srcA = reinterpret_cast<const float4*>(
+              cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
+          const float4* srcJ = reinterpret_cast<const float4*>(
+              cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
+#pragma unroll
+          for (int u = 0; u < EA; ++u) ra[h][u] = srcA[tid + u * NT32];
+#pragma unroll
+          for (int u = 0; u < EJ; ++u) rj[h][u] = srcJ[tid + u * NT32];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float4* dA = reinterpret_cast<float4*>(wA + h * B * MST);
+          float4* dJ = reinterpret_cast<float4*>(wJ + h * B * JST);
+#pragma unroll
+          for (int u = 0; u < EA; ++u) dA[tid + u * NT32] = ra[h][u];
+#pragma unroll
+          for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
+        }
       }
       __syncthreads();
       // full local sweep over the 2B columns
