@@ -308,14 +308,27 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
         }
         __syncthreads();
       }
-      // copy back to the home CTAs
-      for (int h = 0; h < 2; ++h) {
-        float4* dA = reinterpret_cast<float4*>(cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
-        float4* dJ = reinterpret_cast<float4*>(cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
-        const float4* sA = reinterpret_cast<const float4*>(wA + h * B * MST);
-        const float4* sJ = reinterpret_cast<const float4*>(wJ + h * B * JST);
-        for (int e = tid; e < B * MST / 4; e += NT32) dA[e] = sA[e];
-        for (int e = tid; e < B * JST / 4; e += NT32) dJ[e] = sJ[e];
+      // copy back to the home CTAs (local loads first, then remote stores)
+      {
+        float4 ra[2][EA], rj[2][EJ];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4* sA = reinterpret_cast<const float4*>(wA + h * B * MST);
+          const float4* sJ = reinterpret_cast<const float4*>(wJ + h * B * JST);
+#pragma unroll
+          for (int u = 0; u < EA; ++u) ra[h][u] = sA[tid + u * NT32];
+#pragma unroll
+          for (int u = 0; u < EJ; ++u) rj[h][u] = sJ[tid + u * NT32];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float4* dA = reinterpret_cast<float4*>(cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
+          float4* dJ = reinterpret_cast<float4*>(cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
+#pragma unroll
+          for (int u = 0; u < EA; ++u) dA[tid + u * NT32] = ra[h][u];
+#pragma unroll
+          for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
+        }
       }
       if (t == NB - 2 && rot) s_cnt = 1;  // a flag, not a count: only zero matters
       cl.sync();
