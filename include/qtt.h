@@ -330,8 +330,9 @@ qtt_status qtt_last_step_discarded(qtt_ctx* ctx, double* discarded);
 /* Kernel classes counted by qtt_profile: 0 GEMM contraction, 1 Householder
  * QR, 2 Jacobi SVD, 3 sort/truncate (Sec. 4.3 rule), 4 MPO application,
  * 5 MPS sum, 6 copy/transpose, 7 dense FDTD, 8 FP64 refinement of the
- * mixed-precision SVD, 9 other, 10 pivoted QR of the mixed SVD's small R
- * factor (its Jacobi preconditioning). */
+ * mixed-precision SVD, 9 other, 10 the pivoted factor that preconditions the
+ * mixed SVD's Jacobi (Gram matrix and pivoted Cholesky, or pivoted QR of the
+ * small R factor). */
 #define QTT_KCLASSES 11
 
 typedef struct {

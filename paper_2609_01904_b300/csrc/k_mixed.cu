@@ -667,6 +667,176 @@ __global__ void __launch_bounds__(NT32) qrcp_cluster_kernel(const double* __rest
   }
 }
 
+// Order key of a pivot candidate, in integer arithmetic (the FP64 pipe of
+// this part is narrow, comparisons and divisions included): monotone in the
+// value, a NaN above everything, 0 for no candidate.
+__device__ __forceinline__ unsigned long long piv_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b & 0x7fffffffffffffffULL) > 0x7ff0000000000000ULL) return ~0ULL;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+// (ak, ai) ranks above (bk, bi): the larger key, then the smaller index
+__device__ __forceinline__ bool piv_better(unsigned long long ak, int ai, unsigned long long bk, int bi) {
+  return ak > bk || (ak == bk && ai >= 0 && (bi < 0 || ai < bi));
+}
+
+// Cholesky factorisation with diagonal pivoting (Higham, Accuracy and
+// Stability of Numerical Algorithms, 2nd ed., Sec. 10.3) of a symmetric
+// positive semidefinite G (n x n, n <= MN, FP64) in one thread-block cluster.
+// Step k picks the largest remaining diagonal entry d = S_pp of the Schur
+// complement S, emits row k of R, u = S[:, p] / sqrt(d) (zero at the indices
+// already chosen, u_p = sqrt(d)), and subtracts u u^T from S.  The result
+// satisfies R^T R = G up to the dropped remainder: R is the triangular factor
+// of a QR with column pivoting of any M with M^T M = G, with its columns
+// left in their original order (R P is upper trapezoidal).  It stops after
+// kcap rows, or once d <= n 2^-52 d_0 (d_0: the first pivot), the level at
+// which S holds only the rounding of G; k >= 1 rows are always written.
+// Column c of S lives in the shared memory of CTA c % CS; lane s of warp 0
+// keeps the diagonal entry of the CTA's s-th column in a register.  A step:
+// every warp picks the pivot from the candidates (key, index, sqrt(d),
+// 1/sqrt(d)) that all CTAs pushed into this CTA's slots (one per CTA, two
+// alternating slot sets), each thread reads its entry of the pivot column
+// from the owner's shared memory (chosen columns are never written again),
+// warp 0 updates the diagonal and pushes this CTA's next candidate to every
+// CTA while the others update the owned columns, one thread per row; one
+// cluster barrier.  Outputs: R (k x n) row-major with row stride ldr, k at
+// *k_out.
+template <int MN>
+__global__ void __launch_bounds__(MN) pchol_cluster_kernel(const double* __restrict__ G, long long ldg, Dim n_d,
+                                                           Dim kcap_d, int cpc, double* R, long long ldr,
+                                                           int* k_out) {
+  static_assert(MN % 32 == 0 && MN >= 32, "whole warps");
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks();
+  extern __shared__ double smd[];
+  double* col = smd;                     // cpc columns of MN doubles
+  double* u = col + (long long)cpc * MN;  // the current row of R
+  // candidates pushed by the CTAs of the cluster: key, index, sqrt(d), 1/sqrt(d)
+  __shared__ unsigned long long s_ck[2][16];
+  __shared__ int s_ci[2][16];
+  __shared__ double s_cr[2][16], s_cq[2][16];
+  __shared__ int s_done[MN];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long nl = dv(n_d), kc = dv(kcap_d);
+  const int n = (int)(nl < MN ? nl : MN);
+  const int kmax = (int)(kc < n ? kc : n);
+  s_done[tid] = tid >= n;
+  for (int sl = 0; sl < cpc; ++sl) {
+    const int c = rank + sl * CS;
+    col[sl * MN + tid] = (c < n && tid < n) ? G[(long long)c * ldg + tid] : 0.0;
+  }
+  // warp 0, lane s < cpc: the diagonal entry of owned column s
+  const int myc = rank + lane * CS;
+  const bool mine = warp == 0 && lane < cpc && myc < n;
+  double dg = mine ? G[(long long)myc * ldg + myc] : 0.0;
+  // best remaining owned diagonal entry, pushed into slot set b of every CTA
+  auto push = [&](int b) {
+    unsigned long long bk = 0;
+    int bi = -1;
+    double bv = 0.0;
+    if (mine && !s_done[myc]) {
+      bk = piv_key(dg);
+      bi = myc;
+      bv = dg;
+    }
+    for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the best
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      if (piv_better(ok, oi, bk, bi)) {
+        bk = ok;
+        bi = oi;
+        bv = ov;
+      }
+    }
+    double r = 0.0, q = 0.0;
+    if (lane == 0 && bi >= 0) {  // NaN stays NaN; d <= 0 (rounding) gives a zero row
+      r = bv > 0.0 ? sqrt(bv) : (bv == bv ? 0.0 : bv);
+      q = r != 0.0 ? 1.0 / r : 0.0;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (lane < CS) {
+      *cl.map_shared_rank(&s_ck[b][rank], lane) = bk;
+      *cl.map_shared_rank(&s_ci[b][rank], lane) = bi;
+      *cl.map_shared_rank(&s_cr[b][rank], lane) = r;
+      *cl.map_shared_rank(&s_cq[b][rank], lane) = q;
+    }
+  };
+  cl.sync();  // every CTA of the cluster runs before any distributed access
+  if (warp == 0) push(0);
+  cl.sync();
+  unsigned long long thr = 0;  // stop key: n 2^-52 d_0 (none when d_0 is NaN)
+  int k = 0;
+  for (; k < kmax; ++k) {
+    const int b = k & 1;
+    unsigned long long key = 0;  // the same pivot in every warp of every CTA
+    int p = -1, from = lane;
+    if (lane < CS) {
+      key = s_ck[b][lane];
+      p = s_ci[b][lane];
+    }
+    for (int o = 16; o > 0; o >>= 1) {  // every lane: the loop exit is uniform
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, p, o);
+      const int of = __shfl_xor_sync(0xffffffffu, from, o);
+      if (piv_better(ok, oi, key, p)) {
+        key = ok;
+        p = oi;
+        from = of;
+      }
+    }
+    if (p < 0) break;
+    if (k == 0) {
+      if (key != ~0ULL) {
+        const double r0 = s_cr[b][from];
+        thr = piv_key((double)n * 0x1p-52 * (r0 * r0));
+      }
+    } else if (key <= thr) {
+      break;
+    }
+    const double r = s_cr[b][from], q = s_cq[b][from];
+    const double* pc = cl.map_shared_rank(col, p % CS) + (long long)(p / CS) * MN;
+    double ui = 0.0;
+    if (tid == p) ui = r;
+    else if (tid < n && !s_done[tid]) ui = pc[tid] * q;
+    u[tid] = ui;
+    if (tid < n && rank == k % CS) R[(long long)k * ldr + tid] = ui;
+    if (tid == p) s_done[p] = 1;
+    __syncthreads();
+    if (warp == 0) {
+      if (mine && !s_done[myc]) dg = fma(-u[myc], u[myc], dg);
+      push(b ^ 1);
+    }
+#pragma unroll
+    for (int sl = 0; sl < 16; ++sl) {
+      const int c = rank + sl * CS;
+      if (sl >= cpc || c >= n || s_done[c]) continue;
+      col[sl * MN + tid] = fma(-ui, u[c], col[sl * MN + tid]);
+    }
+    cl.sync();
+  }
+  if (k == 0 && kmax > 0) {  // no pivot at all (n = 0 cannot reach here): a zero row
+    if (rank == 0 && tid < n) R[tid] = 0.0;
+    k = 1;
+  }
+  if (rank == 0 && tid == 0 && k_out) *k_out = k;
+  cl.sync();  // no CTA leaves while another may still read its columns
+}
+
+// J[c][a] = W[c][a] / norms[c] (0 where the norm is 0): unit rows
+__global__ void scale_rows_kernel(const double* W, long long ldw, const double* norms, Dim rows_d, Dim cols_d,
+                                  double* J, long long ldj) {
+  const long long rows = dv(rows_d), cols = dv(cols_d);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / cols, a = e % cols;
+    const double nc = norms[c];
+    J[c * ldj + a] = nc != 0.0 ? W[c * ldw + a] / nc : 0.0;
+  }
+}
+
 inline int eg(long long total) {
   long long g = (total + 255) / 256;
   return (int)std::max(1LL, std::min(g, 148LL * 8));
@@ -791,6 +961,37 @@ cudaError_t qrcp_cluster(qtt_ctx* ctx, const double* Ain, long long lda, Dim nr,
   return cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<256>, Ain, lda, nr, nc, cpc, R1, ldr1, Q1, ldq, Vg, k1_out);
 }
 
+static size_t pchol_smem(int cpc) { return ((size_t)cpc * 256 + 256) * sizeof(double); }
+
+cudaError_t pchol_cluster(qtt_ctx* ctx, const double* G, long long ldg, Dim n, Dim kcap, long long nmax, double* R,
+                          long long ldr, int* k_out) {
+  if (nmax > 256 || nmax < 1) return cudaErrorInvalidValue;
+  // at most 16 columns per CTA, at most 16 CTAs (8 CTAs of 32 columns
+  // measured slower: the step is bound by latency, not by the FP64 pipe)
+  const int CS = (int)std::min<long long>(16, std::max<long long>(1, (nmax + 15) / 16));
+  const int cpc = (int)((nmax + CS - 1) / CS);
+  if (cpc > 16) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(256);
+  cfg.stream = ctx->stream;
+  cfg.dynamicSmemBytes = pchol_smem(cpc);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pchol_cluster_kernel<256>, G, ldg, n, kcap, cpc, R, ldr, k_out);
+}
+
+cudaError_t scale_rows(const double* W, long long ldw, const double* norms, Dim rows, Dim cols, long long rmax,
+                       long long cmax, double* J, long long ldj, cudaStream_t st) {
+  scale_rows_kernel<<<eg(rmax * cmax), 256, 0, st>>>(W, ldw, norms, rows, cols, J, ldj);
+  return cudaGetLastError();
+}
+
 cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st) {
   row_norms_kernel<<<(int)std::max(1LL, std::min(nmax, 148LL * 4)), 256, 0, st>>>(W, ldw, n, m, norms);
   return cudaGetLastError();
@@ -819,8 +1020,15 @@ static cudaError_t init_qrcp() {
   return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+static cudaError_t init_pchol() {
+  const void* k = (const void*)pchol_cluster_kernel<256>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pchol_smem(16));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 cudaError_t mixed_init() {
-  cudaError_t (*fs[])() = {init_qrcp, init_jb<1, 1>, init_jb<2, 2>,init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
+  cudaError_t (*fs[])() = {init_qrcp, init_pchol, init_jb<1, 1>, init_jb<2, 2>,init_j32<1, 1>, init_j32<2, 2>, init_j32<3, 3>, init_j32<4, 4>, init_j32<1, 2>,
                            init_j32<2, 1>, init_j32<2, 3>, init_j32<3, 2>, init_j32<3, 4>, init_j32<4, 3>,
                            init_j32<1, 3>, init_j32<1, 4>, init_j32<2, 4>, init_j32<3, 1>, init_j32<4, 1>,
                            init_j32<4, 2>};

@@ -72,6 +72,16 @@ cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, D
 // *k1_out.  Vg: k1 * 256 floats of scratch.
 cudaError_t qrcp_cluster(qtt_ctx* ctx, const double* Ain, long long lda, Dim nr, Dim nc, long long nmax, double* R1,
                          long long ldr1, double* Q1, long long ldq, float* Vg, int* k1_out);
+// Cholesky with diagonal pivoting of a symmetric positive semidefinite G
+// (n x n, ld ldg, n <= nmax <= 256) in one cluster, FP64: R (k x n, row-major,
+// row stride ldr, columns in their original order) with R^T R = G, k <= kcap
+// rows (fewer once the remaining pivots reach the rounding level of G), k at
+// *k_out.
+cudaError_t pchol_cluster(qtt_ctx* ctx, const double* G, long long ldg, Dim n, Dim kcap, long long nmax, double* R,
+                          long long ldr, int* k_out);
+// J[c][a] = W[c][a] / norms[c] for c < rows, a < cols (0 where norms[c] = 0)
+cudaError_t scale_rows(const double* W, long long ldw, const double* norms, Dim rows, Dim cols, long long rmax,
+                       long long cmax, double* J, long long ldj, cudaStream_t st);
 cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st);
 cudaError_t mixed_init();
 

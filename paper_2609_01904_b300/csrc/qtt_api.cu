@@ -463,6 +463,42 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     return fail(QTT_EINVAL, "internal: SVD larger than the workspace");
   double* sig = sigma_out ? sigma_out : s.d_sig;
   int* kq = s.d_ints + 0;
+  // The Gram matrix costs nv^2 ell FP64 FMAs, the QR about 4 us per column
+  // (its chain of reflectors): up to nv ell = 2^20 the Gram route is cheaper.
+  if (ellmax > nvmax && ctx->use_mp && nvmax <= 256 && ldv * nvmax <= s.tv && nvmax * ellmax <= (1LL << 20)) {
+    // Preconditioned Jacobi (Drmac & Veselic 2008) on the rows of the
+    // triangular factor of a QR with column pivoting of M, formed without
+    // touching M again: G = M^T M in FP64, G = R^T R by Cholesky with
+    // diagonal pivoting (R graded, k rows: the numerical rank), one-sided
+    // Jacobi on the rows of R (~7 sweeps instead of ~25), J R = W with
+    // orthogonal rows.  M = Q R = (Q J^T) W, so sigma = |W_c| and the right
+    // singular vectors of M are the rows of W / |W_c|, re-orthonormalised in
+    // FP64.
+    int* kr = s.d_ints + 1;
+    GemmArgs g = gemm0();  // G[a][c] = sum_l Tv[a][l] Tv[c][l]
+    g.A = Tv;
+    g.B = Tv;
+    g.C = s.d_tt;
+    g.M = nv;
+    g.N = nv;
+    g.K = ell;
+    g.sai = ell;
+    g.sak = dconst(1);
+    g.sbk = dconst(1);
+    g.sbj = ell;
+    g.sci = dconst(ldv);
+    g.scj = dconst(1);
+    KL(KC_PIVOT, gemm_f64(g, nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_PIVOT, pchol_cluster(ctx, s.d_tt, ldv, nv, ell, nvmax, s.d_rv, ldv, kr));
+    CKS(jacobi_any(ctx, s.d_rv, ldv, dptr(kr), nv, nvmax, nvmax, s.d_jv, ldv, s.d_norm));
+    // jacobi_any leaves W = J R in the refinement buffer
+    KL(KC_REFINE, scale_rows(s.d_rw, ldv, s.d_norm, dptr(kr), nv, nvmax, nvmax, s.d_jh, ldv, ctx->stream));
+    CKS(ns_rows(ctx, s.d_jh, ldv, dptr(kr), nv, nvmax, nvmax));
+    CKS(ns_rows(ctx, s.d_jh, ldv, dptr(kr), nv, nvmax, nvmax));
+    KL(KC_POST, svd_post(ctx, s.d_norm, dptr(kr), nv, nv, s.d_jh, ldv, eps, chi, rank_cap, rank_out, sig, disc_out,
+                         Jp, Jt, nsv_out));
+    return QTT_OK;
+  }
   if (ellmax > nvmax && ctx->use_mp && nvmax <= 256 && ldv * nvmax <= s.tv && nvmax * 128 <= s.tv) {
     // Preconditioned Jacobi (Drmac & Veselic 2008): M = Q R0 (R0 only),
     // R0^T P = Q1 R1 with column pivoting in one cluster, one-sided Jacobi
@@ -472,7 +508,7 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     // orthogonal factors, re-orthonormalised in FP64.
     int* k1 = s.d_ints + 1;
     KL(KC_QR, qr_any(ctx, Tv, ell, s.d_tq, ellmax, ell, nv, nvmax, s.d_rv, false, nullptr, kq, ldv, 0));
-    KL(KC_QRCP, qrcp_cluster(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, s.d_tt, ldv, s.d_qt, ldv,
+    KL(KC_PIVOT, qrcp_cluster(ctx, s.d_rv, ldv, nv, dptr(kq), nvmax, s.d_tt, ldv, s.d_qt, ldv,
                            reinterpret_cast<float*>(s.d_tq), k1));
     CKS(jacobi_any(ctx, s.d_tt, ldv, dptr(k1), dptr(kq), nvmax, nvmax, s.d_jv, ldv, s.d_norm));
     GemmArgs g = gemm0();  // J_M[c][a] = sum_k J[c][k] Q1[a][k]

@@ -225,7 +225,7 @@ struct Workspace {
 }  // namespace qtt
 
 namespace qtt {
-enum { KC_GEMM = 0, KC_QR, KC_JACOBI, KC_POST, KC_MPO, KC_SUM, KC_COPY, KC_FDTD, KC_REFINE, KC_OTHER, KC_QRCP, KC_N };
+enum { KC_GEMM = 0, KC_QR, KC_JACOBI, KC_POST, KC_MPO, KC_SUM, KC_COPY, KC_FDTD, KC_REFINE, KC_OTHER, KC_PIVOT, KC_N };
 
 struct Prof {
   int timing = 0;

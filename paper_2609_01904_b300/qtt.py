@@ -49,7 +49,7 @@ _PL = ctypes.POINTER(ctypes.c_long)
 
 QTT_KCLASSES = 11
 KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "copy", "fdtd", "refine", "other",
-                  "qrcp"]
+                  "pivot"]
 
 
 class qtt_profile(ctypes.Structure):

@@ -180,3 +180,51 @@ def test_fp32_form_steps_from_a_mid_run_state_of_the_64_shot_workload(q):
         err = _rel(_dense(q, cur, N), O.mps_to_dense(want, n, wl.order))
         assert err < min(_tol(st), 1e-3), (k, err, _tol(st))
         po, co = co, want
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_from_the_zero_state_is_the_source_alone(q, prec):
+    """Both states zero: every truncation SVD of the step factors a zero or a
+    rank-one matrix (zero pivots, zero vectors), and the step leaves the
+    source term alone (Eq. 17 with psi = 0)."""
+    n, chi, eps = 5, 16, 1e-7
+    N = 1 << n
+    c = W.layered_model(n, 40.0, 11)
+    lam2 = (0.5 / c.max()) ** 2
+    ctx = q.qtt_ctx_create(n=n, chi_max=chi, eps=eps, chi_c=12, eps_c=1e-8, prec=prec)
+    L = q.qtt_laplacian_mpo(ctx)
+    C = q.qtt_velocity_mps(ctx, _t(c))
+    prev, cur = q.qtt_mps_create_zero(ctx), q.qtt_mps_create_zero(ctx)
+    src, amp = (N // 2 + 1, 3), 0.37
+    q.qtt_step(L, C, lam2, prev, cur, src, amp)
+    got = _dense(q, cur, N)
+    want = np.zeros((N, N))
+    want[src] = amp
+    # FP32 form: the amplitude passes the FP32 QR sweep of the round
+    assert np.abs(got - want).max() <= (1e-12 if prec == "fp64" else 1e-6) * amp
+    assert q.qtt_mps_ranks(cur) == [1] * (2 * n + 1)
+    # and with no source at all the state stays exactly zero
+    z = q.qtt_mps_create_zero(ctx)
+    q.qtt_step(L, C, lam2, prev, z, src, 0.0)
+    assert not _dense(q, z, N).any()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_non_finite_state_is_reported(q, prec):
+    """A NaN in the state reaches a singular-value spectrum and the context
+    reports QTT_ENONFINITE at the next synchronisation (no silent result)."""
+    n, chi = 5, 16
+    c = W.layered_model(n, 40.0, 11)
+    lam2 = (0.5 / c.max()) ** 2
+    ctx = q.qtt_ctx_create(n=n, chi_max=chi, eps=1e-7, chi_c=12, eps_c=1e-8, prec=prec)
+    L = q.qtt_laplacian_mpo(ctx)
+    C = q.qtt_velocity_mps(ctx, _t(c))
+    prev_h = O.tt_round(W.random_tt_cores(2 * n, chi, 1, decay=0.05), 1e-14, chi)
+    cur_h = O.tt_round(W.random_tt_cores(2 * n, chi, 2, decay=0.05), 1e-14, chi)
+    cur_h[n][0, 1, 0] = np.nan
+    prev = q.qtt_mps_from_cores(ctx, prev_h)
+    cur = q.qtt_mps_from_cores(ctx, cur_h)
+    with pytest.raises(q.QttError) as e:
+        q.qtt_step(L, C, lam2, prev, cur, (3, 3), 0.37)
+        q.qtt_ctx_sync(ctx)
+    assert e.value.status == q.QTT_ENONFINITE
