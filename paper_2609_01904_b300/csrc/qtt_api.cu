@@ -422,7 +422,7 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
     CKS(ns());
     KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
     KL(KC_REFINE, gemm_f64(gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
-    KL(KC_REFINE, omega_factor(s.d_rg, norms, s.d_rh, ld, nv, nvmax, ctx->stream));  // norms: scratch here
+    KL2(KC_REFINE, omega_factor(s.d_rg, norms, s.d_rh, ld, nv, nvmax, ctx->stream));  // two kernels; norms: scratch
     KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
     KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
                          ctx->stream));
