@@ -1,6 +1,12 @@
 // Mixed-precision SVD of a small square bond factor (the reduced-precision
 // form of the step).
 //
+// Stage 0, the preconditioning factor (Drmac & Veselic 2008): a graded
+// triangular R whose rows are the Jacobi vectors, from a Cholesky with
+// diagonal pivoting of the FP64 Gram matrix (pchol_cluster_kernel) or from a
+// Householder QR with column pivoting of the small R0^T of a QR of the bond
+// matrix (qrcp_cluster_kernel), each inside one thread-block cluster.
+//
 // Stage 1, FP32: one-sided Jacobi on the nv column vectors, all of them held
 // in the shared memory of one thread-block cluster (columns split across the
 // CTAs, partners reached through distributed shared memory), one hardware

@@ -451,7 +451,10 @@ qtt_status ns_rows(qtt_ctx* ctx, double* J, long long ldj, Dim rows, Dim cols, l
 // not modified).  J (nv x r) holds the kept right singular vectors of the
 // matrix M whose columns are the vectors: M J = U S.  Writes the kept rank
 // to rank_out, Jp = J^T (r x nv) and Jt = J (nv x r).  The Jacobi sweeps
-// always run on a square problem of size min(nv, ell):
+// always run on a square problem of size at most min(nv, ell):
+//   reduced-precision form, ell > nv (nv <= 256): the rows of a pivoted
+//     triangular factor R of M (from the Gram matrix, or from a QR and a
+//     pivoted QR of the small R0^T), rotated in FP32 and refined in FP64;
 //   ell >= nv: M = Q R, rotate the columns of R (Q never formed);
 //   ell <  nv: M^T = Q R, rotate the rows of R, J = Q J_R.
 qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvmax, long long ellmax, double eps,
