@@ -129,6 +129,20 @@ def _setup_gpu_state(q, wl, ctx, c, amps, stream):
     return C, L, prev, cur
 
 
+def job_rate(t_total_ms: float, steps: int, world: int, device: str = "cuda") -> tuple[float, float]:
+    """Whole-job rate of a timed region: the maximum of the ranks' times
+    (all_reduce MAX over the process group when world > 1, then a barrier)
+    and world * steps / that time.  Returns (max time in ms, steps/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total_ms = float(tt.item())
+        dist.barrier()
+    return t_total_ms, world * steps / (t_total_ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2609_01904_b300 import qtt as q
@@ -191,13 +205,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms_per_step = float(np.mean(step_ms))
     t_total = float(np.sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-        dist.barrier()
-    value = world * args.steps / (t_total / 1e3)
+    t_total, value = job_rate(t_total, args.steps, world)
 
     # end to end through the public API: the step's input (the source sample)
     # from pinned host memory, the receiver trace read back to pinned host
