@@ -489,6 +489,83 @@ def mps_step(L: list[np.ndarray], c2: list[np.ndarray], lambda2: float,
 
 
 # ---------------------------------------------------------------------------
+# Fused transition operator (Eq. 7): A = 2I + lambda^2 C^2 L
+# ---------------------------------------------------------------------------
+def mpo_product(W_out: list[np.ndarray], W_in: list[np.ndarray]) -> list[np.ndarray]:
+    """MPO of the operator product W_out W_in (W_in acts first): core k is
+    sum_u W_out[a][t][u][a'] W_in[b][u][s][b'] on the bond pairs (a, b)."""
+    out = []
+    for A, B in zip(W_out, W_in):
+        P = np.einsum("atub,cusd->actsbd", A, B)
+        out.append(P.reshape(A.shape[0] * B.shape[0], 2, 2, A.shape[3] * B.shape[3]))
+    return out
+
+
+def mpo_sum(terms: list[tuple[float, list[np.ndarray]]]) -> list[np.ndarray]:
+    """sum_j c_j W_j as one MPO, built like :func:`mps_sum`: first cores side
+    by side with the coefficients, middle cores block-diagonal, last cores
+    stacked."""
+    d = len(terms[0][1])
+    out = []
+    for k in range(d):
+        blocks = [t[1][k] for t in terms]
+        L = 1 if k == 0 else sum(b.shape[0] for b in blocks)
+        R = 1 if k == d - 1 else sum(b.shape[3] for b in blocks)
+        core = np.zeros((L, 2, 2, R))
+        lo = ro = 0
+        for (coef, _), b in zip(terms, blocks):
+            l, _, _, r = b.shape
+            if k == 0:
+                core[:, :, :, ro:ro + r] += coef * b
+            elif k == d - 1:
+                core[lo:lo + l] += b
+            else:
+                core[lo:lo + l, :, :, ro:ro + r] = b
+            lo += l if k > 0 else 0
+            ro += r if k < d - 1 else 0
+        out.append(core)
+    return out
+
+
+def a_operator_mpo(L: list[np.ndarray], c2: list[np.ndarray], lambda2: float) -> list[np.ndarray]:
+    """MPO of the transition operator of Eq. 7, A = 2I + lambda^2 C^2 L: the
+    diagonal MPO of c^2 (Sec. 4.3) times the Laplacian MPO (Eq. 16), plus
+    twice the identity; bond r_c w + 1.
+
+    Balancing (a reading: the paper gives no representation of A): the c^2
+    MPS keeps its whole norm (~c_max^2, 1e6..1e7 m^2/s^2) in its last core, so
+    the product term would be ~lambda^2 ~ 1e-8 against the identity's 1 at
+    every bond the zip-up cuts, and FP64 rounding of the cut would be
+    amplified by the last core.  The norm nu of the last c^2 core is moved
+    into the coefficient: lambda^2 nu on the first core, the last c^2 core
+    divided by nu.  The operator is unchanged."""
+    d = len(L)
+    B = [np.array(x, dtype=np.float64) for x in c2]
+    nu = float(np.linalg.norm(B[-1]))
+    if nu > 0.0:
+        B[-1] = B[-1] / nu
+    else:
+        nu = 1.0
+    return mpo_sum([(lambda2 * nu, mpo_product(diagonal_mpo(B), L)), (2.0, [np.eye(2).reshape(1, 2, 2, 1)] * d)])
+
+
+def mps_step_fused(A: list[np.ndarray], prev: list[np.ndarray], cur: list[np.ndarray], eps: float, chi: int,
+                   src: tuple[int, int] | None = None, amp: float = 0.0, n: int | None = None,
+                   order: str | None = None, stats: list | None = None) -> list[np.ndarray]:
+    """The step of Eq. 7 with A applied as one operator:
+        phi       = A psi^k                 (zip-up of A, sites 1 -> d)
+        theta     = phi - psi^{k-1} [+ amp * e_src]
+        psi^{k+1} = round(theta).
+    In exact arithmetic this is the step of :func:`mps_step`; the truncation
+    points differ (one zip-up instead of two)."""
+    phi = zipup_lr(A, cur, eps, chi, stats)
+    terms = [(1.0, phi), (-1.0, prev)]
+    if src is not None:
+        terms.append((amp, product_state(src[0], src[1], n, order)))
+    return tt_round(mps_sum(terms), eps, chi, stats)
+
+
+# ---------------------------------------------------------------------------
 # Dense FDTD (Sec. 2, Eq. 2)
 # ---------------------------------------------------------------------------
 def neighbour_sum(u: np.ndarray, bc: str) -> np.ndarray:

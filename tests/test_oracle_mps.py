@@ -251,3 +251,81 @@ def test_leapfrog_energy_is_conserved_by_untruncated_mps_step(bc):
         prev, cur = cur, O.mps_step(L, C, lam2, prev, cur, 0.0, INF)
     E = O.leapfrog_energy(O.mps_to_dense(prev, n, order), O.mps_to_dense(cur, n, order), c2r, lam2, bc)
     assert abs(E - E0) < 1e-11 * abs(E0)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_transition_operator_mpo_is_the_dense_eq7_operator(order, bc):
+    """Eq. 7: the MPO of A = 2I + lambda^2 C^2 L contracted to a matrix is
+    2 I + lambda^2 diag(c^2) (5-point stencil), built here by brute force from
+    the grid (neighbours by index arithmetic, not from any MPO)."""
+    n = 2
+    N = 1 << n
+    rng = np.random.default_rng(8)
+    c = rng.uniform(1500.0, 3000.0, (N, N))
+    lam2 = (0.4 / c.max()) ** 2
+    C = O.velocity_mps(c, n, order, 0.0, INF)
+    A = O.a_operator_mpo(O.laplacian_mpo(n, order, bc), C, lam2)
+    w = O.laplacian_mpo(n, order, bc)
+    rc = O.mps_ranks(C)
+    assert [1] + [a.shape[3] for a in A] == [1] + [rc[k + 1] * w[k].shape[3] + 1 for k in range(2 * n - 1)] + [1]
+    lap = np.zeros((N * N, N * N))
+    for x in range(N):
+        for z in range(N):
+            i = x * N + z
+            lap[i, i] -= 4.0
+            for dx, dz in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                xx, zz = x + dx, z + dz
+                if bc == "periodic":
+                    lap[i, (xx % N) * N + zz % N] += 1.0
+                elif 0 <= xx < N and 0 <= zz < N:
+                    lap[i, xx * N + zz] += 1.0
+    want = 2.0 * np.eye(N * N) + lam2 * np.diag((c * c).reshape(-1)) @ lap
+    got = O.grid_operator(A, n, order)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_untruncated_fused_step_equals_fdtd(order, bc):
+    """Table 1 with the operator of Eq. 7 applied in one zip-up: chi = inf,
+    eps = 0 reproduces Eq. 2."""
+    n = 3
+    rng = np.random.default_rng(9)
+    c = rng.uniform(1500.0, 3000.0, (8, 8))
+    lam2 = (0.5 / c.max()) ** 2
+    C = O.velocity_mps(c, n, order, 0.0, INF)
+    c2r = O.mps_to_dense(C, n, order)
+    A = O.a_operator_mpo(O.laplacian_mpo(n, order, bc), C, lam2)
+    d = 2 * n
+    prev, cur = O.zero_mps(d), O.zero_mps(d)
+    up, uc = np.zeros((8, 8)), np.zeros((8, 8))
+    src = (2, 6)
+    for k in range(25):
+        amp = math.cos(0.2 * k) + 0.05 * k
+        nxt = O.mps_step_fused(A, prev, cur, 0.0, INF, src, amp, n, order)
+        un = O.fdtd_step(up, uc, c2r, lam2, bc, src, amp)
+        prev, cur = cur, nxt
+        up, uc = uc, un
+    assert np.linalg.norm(O.mps_to_dense(cur, n, order) - uc) / np.linalg.norm(uc) < 1e-12
+
+
+def test_fused_and_two_zipup_steps_agree_to_the_truncation():
+    """Both forms of the truncated step approximate the same Eq. 7 update:
+    from one seeded state, with eps = 1e-9 and no binding cap, they agree to
+    the truncation level (the difference is the zip-up truncations, each below
+    eps relative to its bond)."""
+    n, order, bc = 4, "interleaved", "periodic"
+    N = 1 << n
+    rng = np.random.default_rng(10)
+    c = rng.uniform(1500.0, 3000.0, (N, N))
+    lam2 = (0.5 / c.max()) ** 2
+    C = O.velocity_mps(c, n, order, 1e-12, INF)
+    Lm = O.laplacian_mpo(n, order, bc)
+    A = O.a_operator_mpo(Lm, C, lam2)
+    u0, u1 = rng.standard_normal((N, N)), rng.standard_normal((N, N))
+    prev = O.state_from_dense(u0, n, order, 1e-12, INF)
+    cur = O.state_from_dense(u1, n, order, 1e-12, INF)
+    a = O.mps_to_dense(O.mps_step(Lm, C, lam2, prev, cur, 1e-9, INF, (3, 4), 0.5, n, order), n, order)
+    b = O.mps_to_dense(O.mps_step_fused(A, prev, cur, 1e-9, INF, (3, 4), 0.5, n, order), n, order)
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-7
