@@ -36,8 +36,12 @@ METRIC = "MPS steps/s at 2^20 grid, chi=128, rel-L2<=1e-3: chosen form vs plain 
 UNIT = "steps/s"
 WORKLOAD_IDX = 2
 MID_RUN = 2000
-FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 (148 SMs x 2032 MHz x ~4.2 FLOP/clk/SM)
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 FMA pipes at the maximum SM clock
+# shared by both arms: the workload, its state and the timing protocol
+def workload_config(wl, state_step: int) -> dict:
+    return {"workload": wl.name, "n": wl.n, "grid": f"{wl.N}x{wl.N}", "chi_max": wl.chi, "eps": wl.eps,
+            "chi_c": wl.chi_c, "eps_c": wl.eps_c, "order": wl.order, "bc": wl.bc,
+            "source": list(wl.sources[0]), "state": f"mid-run (step {state_step} of {wl.steps}), ranks saturated",
+            "l2": "GPU arm: flushed between timed steps (256 MiB write); host arm: no L2 flush"}
 
 
 def _peaks():
@@ -107,9 +111,10 @@ class ClockSampler:
         return out
 
 
-def _setup_gpu_state(q, wl, ctx, c, amps, stream):
+def _setup_gpu_state(q, wl, ctx, c, amps, stream, mid_run=None):
     """Velocity MPS, Laplacian MPO, and the mid-run state (dense FDTD on the
     GPU to MID_RUN, then TT-SVD + round in the library)."""
+    mid_run = MID_RUN if mid_run is None else mid_run
     import torch
     N = wl.N
     with torch.cuda.stream(stream):
@@ -120,7 +125,7 @@ def _setup_gpu_state(q, wl, ctx, c, amps, stream):
         up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
         uc, un = up.clone(), up.clone()
         lam2 = wl.lambda2(c)
-        for k in range(MID_RUN):
+        for k in range(mid_run):
             q.qtt_fdtd_step(ctx, c2, lam2, up, uc, un, wl.sources[0], float(amps[k]))
             up, uc, un = uc, un, up
         prev = q.qtt_mps_from_dense(ctx, up)
@@ -143,6 +148,81 @@ def job_rate(t_total_ms: float, steps: int, world: int, device: str = "cuda") ->
     return t_total_ms, world * steps / (t_total_ms / 1e3)
 
 
+def measured_peaks(q, stream) -> dict:
+    """Peaks of the pipes the step's kernels run on: FP32 and FP64 FMA rates
+    measured on this device by the library's probe; the tensor pipe and HBM
+    from MEASURED_PEAKS.json (TF32 = half the measured dense BF16 rate, the
+    nominal ratio)."""
+    mp = _peaks()
+    with_stream = {"fp32": q.qtt_peak_probe("fp32", stream), "fp64": q.qtt_peak_probe("fp64", stream)}
+    bf16 = mp.get("bf16_tflops_sustained") or mp.get("bf16_tflops")
+    return {"fp32_tflops": with_stream["fp32"], "fp64_tflops": with_stream["fp64"],
+            "bf16_tflops": bf16, "tf32_tflops": (bf16 / 2.0) if bf16 else None, "hbm_gbs": mp.get("hbm_gbs"),
+            "source": "fp32/fp64: qtt_peak_probe (FMA chains, 32 warps per SM, ~60 ms); bf16: MEASURED_PEAKS.json "
+                      "sustained cuBLAS GEMM; tf32 = bf16 / 2 (nominal ratio)"}
+
+
+# pipe each kernel class runs on, per form (classes without counted work are
+# memory- or latency-bound copies and small kernels)
+_PIPE = {
+    "fp64": {"gemm": "fp64", "qr": "fp64", "jacobi": "fp64", "refine": "fp64", "pivot": "fp64"},
+    "fp32": {"gemm": "fp32", "qr": "fp32", "jacobi": "fp32", "refine": "fp64", "pivot": "fp64"},
+    "tf32": {"gemm": "tf32", "qr": "fp32", "jacobi": "fp32", "refine": "fp64", "pivot": "fp64"},
+    "bf16": {"gemm": "bf16", "qr": "fp32", "jacobi": "fp32", "refine": "fp64", "pivot": "fp64"},
+}
+
+
+def roofline(prof: dict, prof_steps: int, ms_per_step: float, form: str, peaks: dict) -> dict:
+    """The dominant class with its achieved rate against its pipe's peak, and
+    the step-level fraction sum_phase(work / peak) / step time."""
+    ms, fl, launches = prof["ms"], dict(prof["flops"]), prof["launches"]
+    fl["jacobi"] = fl.get("jacobi", 0.0) + prof["svd_flops"]  # SVD work of the logged Jacobi launches
+    pipes = _PIPE[form]
+    phases, ideal_s = {}, 0.0
+    for cls, t in ms.items():
+        if t <= 0:
+            continue
+        work = fl.get(cls, 0.0) / prof_steps
+        pipe = pipes.get(cls)
+        peak = peaks.get(f"{pipe}_tflops") if pipe else None
+        ph = {"ms_per_step": round(t / prof_steps, 3), "work_flop_per_step": work, "pipe": pipe, "peak_tflops": peak}
+        if pipe and peak and work > 0:
+            ph["achieved_tflops"] = work / (t / prof_steps / 1e3) / 1e12
+            ph["frac"] = ph["achieved_tflops"] / peak
+            ideal_s += work / (peak * 1e12)
+        phases[cls] = ph
+    dom = max(ms, key=lambda kk: ms[kk])
+    pipe = pipes.get(dom)
+    peak = peaks.get(f"{pipe}_tflops") if pipe else None
+    achieved = fl.get(dom, 0.0) / (ms[dom] / 1e3) / 1e12 if ms[dom] > 0 else None
+    kernel = {"jacobi": "jacobi32_block_kernel (one-sided Jacobi SVD, FP32, one cluster)" if form != "fp64"
+              else "jacobi_kernel (one-sided Jacobi SVD, FP64, cooperative)"}.get(dom, dom)
+    roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "peak_source": f"measured {pipe} FMA rate of this device (qtt_peak_probe)" if pipe in ("fp32", "fp64")
+            else "MEASURED_PEAKS.json",
+            "traffic": None, "launches": launches.get(dom, 0) // max(prof_steps, 1),
+            "avg_launch_ms": ms[dom] / max(launches.get(dom, 1), 1),
+            "avg_sweeps": prof["svd_sweeps"] / max(prof["svd_logged"], 1),
+            "work": "SVD: 6 m n^2 + 20 n^3 per Jacobi launch on its n x m factor (Golub-Van Loan); GEMM: 2 M N K; "
+                    "Householder QR: 2 p k^2 - 2 k^3/3 (+ the same for a thin Q); counted on the device per launch",
+            "share_of_step": ms[dom] / max(sum(ms.values()), 1e-9),
+            "step_fraction": ideal_s / (ms_per_step / 1e3),
+            "step_fraction_note": "sum over phases of algorithmic work / peak of its pipe, over the measured step "
+                                  "time (the graph-replayed step); classes without counted work (sorts, copies, "
+                                  "MPO application, sums, the cluster Cholesky / pivoted QR) add time but no work",
+            "phases": phases, "peaks": peaks}
+    if dom == "jacobi" and form != "fp64":
+        # DRAM bytes of one 256-vector launch of the FP32 block Jacobi, from an
+        # ncu capture of this kernel on the same workload (the input matrix,
+        # read once); per launch, like `achieved`
+        roof["traffic"] = 592.9e3
+        roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of one jacobi32_block_kernel launch "
+                                "(ncu --set full -k regex:jacobi32_block -c 3 on python bench.py --steps 1 --warmup 3 "
+                                "--compare 0 --no-cpu-baseline)")
+    return roof
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2609_01904_b300 import qtt as q
@@ -162,6 +242,19 @@ def run_ours(args, rank, world, local_rank):
     src = wl.sources[0]
     step = q.qtt_step_graph if args.graph else q.qtt_step
     k = MID_RUN
+    tune = None
+    if args.autotune:
+        # launch shapes of this workload and form, measured on its mid-run
+        # state (cached per device, form and shape in a JSON file)
+        path = os.path.join(tempfile.gettempdir(), f"qtt_autotune_{wl.name}_{args.form}.json")
+        t0 = time.time()
+        with torch.cuda.stream(stream):
+            nb = q.qtt_autotune(L, C, lam2, prev, cur, path, reps=3)
+        with open(path) as f:
+            tj = json.load(f)
+        tune = {"buckets": nb, "seconds": round(time.time() - t0, 2), "choices": [
+            {"op": "gemm" if e["op"] == 0 else "qr", "kind": e["kind"], "bucket": [e["a"], e["b"], e["c"]],
+             "choice": e["choice"], "us_per_launch": e["us_per_launch"]} for e in tj["entries"]]}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step(L, C, lam2, prev, cur, src, float(amps[k]))
@@ -228,34 +321,12 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     ranks1 = q.qtt_mps_ranks(cur)
 
-    # roofline of the dominant kernel class, from the live event timing
-    ms = prof["ms"]
-    dom = max(ms, key=lambda kk: ms[kk])
-    launches = prof["launches"]
-    svd_flops = prof["svd_flops"]
-    roof = {"bound": "alu", "traffic": None, "launches": launches.get(dom, 0),
-            "avg_launch_ms": ms[dom] / max(launches.get(dom, 1), 1),
-            "avg_sweeps": prof["svd_sweeps"] / max(prof["svd_logged"], 1),
-            "work": "6 m n^2 + 20 n^3 per SVD of the reduced n x m factor (Golub-Van Loan), sizes logged per launch"}
-    if dom == "jacobi" and args.form == "fp64":
-        achieved = svd_flops / (ms["jacobi"] / 1e3) / 1e12
-        roof.update({"kernel": "jacobi_kernel (one-sided Jacobi SVD, FP64, cooperative)", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal FP64 of the recipe (1.25 TFLOP/s); FP64 FMA probe measured 0.95"})
-    elif dom == "jacobi":
-        achieved = svd_flops / (ms["jacobi"] / 1e3) / 1e12
-        # DRAM bytes of one 256-vector launch from the ncu capture of the
-        # current kernel (profiles/jacobi32_block_qtt1024_marmousi.md)
-        roof["traffic"] = 592.9e3
-        roof["traffic_note"] = "dram read+write of one 256-vector launch (ncu); the input, read once"
-        roof.update({"kernel": "jacobi32_block_kernel (one-sided Jacobi SVD, FP32, one cluster)",
-                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS,
-                     "peak_source": "FP32 FMA: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz; probe measured 63"})
-    else:
-        roof.update({"kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None})
-    roof["share_of_step"] = ms[dom] / max(sum(ms.values()), 1e-9)
-    roof["class_ms_per_step"] = {kk: round(v / prof_steps, 3) for kk, v in ms.items() if v > 0}
+    # roofline: the dominant kernel class, and the whole step as the sum over
+    # phases of algorithmic work / peak of the pipe that phase runs on,
+    # divided by the measured step time (class times and work from the two
+    # launched steps with per-launch events and device-side work counters)
+    peaks = measured_peaks(q, stream)
+    roof = roofline(prof, prof_steps, ms_per_step, args.form, peaks)
 
     n_launch = int(sum(launches_timed.values()))
 
@@ -296,15 +367,14 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.form == "fp64" else "f32+f64",
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "tf32x3": "tf32x3+f32+f64", "tf32": "tf32+f32+f64",
+                  "bf16": "bf16+f32+f64"}[args.form],
         "data": "synthetic (seeded Marmousi-shaped velocity section; Ricker source)",
-        "config": {"workload": wl.name, "n": wl.n, "grid": f"{wl.N}x{wl.N}", "chi_max": wl.chi, "eps": wl.eps,
-                   "chi_c": wl.chi_c, "eps_c": wl.eps_c, "order": wl.order, "bc": wl.bc, "form": args.form,
-                   "state": f"mid-run (step {MID_RUN} of {wl.steps})", "ranks_start": ranks0,
-                   "graph": bool(args.graph),
-                   "ranks_end": ranks1, "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}", "grid_point_updates_per_s": value * wl.N * wl.N,
-                   "setup_s": round(setup_s, 2)},
+        "config": workload_config(wl, MID_RUN),
+        "form": args.form,
+        "run": {"ranks_start": ranks0, "ranks_end": ranks1, "graph": bool(args.graph), "autotune": tune,
+                "parallelism": f"replicas x{world}", "grid_point_updates_per_s": value * wl.N * wl.N,
+                "setup_s": round(setup_s, 2)},
         "gpu_launches": n_launch,
         "e2e": {"value": args.e2e_steps / e2e_s * world if args.e2e_steps else None, "unit": UNIT,
                 "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 8 * len(wl.receivers)},
@@ -403,7 +473,8 @@ def run_shots(args):
         "metric": "MPS shot-steps/s, 64 shots on a 2^18 grid, per-shot chi in {32,64,128,256} (1 B300)",
         "value": value, "unit": "shot-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.form == "fp64" else "f32+f64", "data": "synthetic (seeded layered section)",
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "tf32x3": "tf32x3+f32+f64", "tf32": "tf32+f32+f64",
+                  "bf16": "bf16+f32+f64"}[args.form], "data": "synthetic (seeded layered section)",
         "config": {"workload": wl.name, "n": wl.n, "shots": ns, "chi_per_shot": chis, "eps": wl.eps,
                    "graph": bool(args.graph),
                    "form": args.form, "state": f"mid-run (step {SHOTS_MID_RUN})", "max_rank_start": ranks0,
@@ -417,6 +488,426 @@ def run_shots(args):
     }
 
 
+def write_png_pair(path: str, left: np.ndarray, right: np.ndarray) -> None:
+    """Two fields side by side as an 8-bit grayscale PNG (zero = mid-grey,
+    both scaled by the 99.5th percentile of |left|), plain file output."""
+    import struct
+    import zlib
+    vmax = float(np.percentile(np.abs(left), 99.5)) or 1.0
+    gap = np.full((left.shape[1], 4), 255, dtype=np.uint8)
+
+    def img(u):  # u[x, z]: rows = depth z, columns = x
+        return np.clip(128.0 + 127.0 * u.T / vmax, 0, 255).astype(np.uint8)
+
+    a = np.concatenate([img(left), gap, img(right)], axis=1)
+    raw = b"".join(b"\x00" + row.tobytes() for row in a)
+
+    def chunk(tag, data):
+        return struct.pack(">I", len(data)) + tag + data + struct.pack(">I", zlib.crc32(tag + data) & 0xFFFFFFFF)
+
+    png = (b"\x89PNG\r\n\x1a\n" + chunk(b"IHDR", struct.pack(">IIBBBBB", a.shape[1], a.shape[0], 8, 0, 0, 0, 0))
+           + chunk(b"IDAT", zlib.compress(raw, 9)) + chunk(b"IEND", b""))
+    with open(path, "wb") as f:
+        f.write(png)
+
+
+def run_paper(args):
+    """The paper's own run (Sec. 5) on the synthetic stand-in: 256 x 256,
+    dh = 10 m, dt = 1 ms, impulsive source of strength 1 at the centre as the
+    initial condition, chi = 128, eps = 1e-7, 300 steps; MPS steps/s over the
+    whole run, the per-step time curve, and the MPS field against the dense
+    Eq. 2 run on the same GPU (with the compressed c^2 the MPS uses, and with
+    the exact c^2)."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    wl = W.paper_run()
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    N, steps = wl.N, wl.steps
+    src = wl.sources[0]
+    stream = torch.cuda.Stream()
+    ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                           eps_c=wl.eps_c, prec=args.form, stream=stream)
+    with torch.cuda.stream(stream):
+        c_dev = torch.as_tensor(c, device="cuda")
+        C = q.qtt_velocity_mps(ctx, c_dev)
+        L = q.qtt_laplacian_mpo(ctx)
+        prev, cur = q.qtt_mps_create_zero(ctx), q.qtt_mps_create_zero(ctx)
+        q.qtt_inject_source(cur, src[0], src[1], 1.0)  # u^0 = e_src, u^-1 = 0
+    step = q.qtt_step_graph if args.graph else q.qtt_step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ranks = []
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            for k in range(steps):
+                step(L, C, lam2, prev, cur, None, 0.0)
+                evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    total_s = evs[0].elapsed_time(evs[steps]) / 1e3
+    ranks = q.qtt_mps_ranks(cur)
+    mps = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    c2m = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    q.qtt_to_dense(cur, mps)
+    q.qtt_to_dense(C, c2m)
+    c2 = c_dev * c_dev
+    fields = {}
+    for name, c2f in (("compressed_c2", c2m), ("exact_c2", c2)):
+        up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        uc = up.clone()
+        uc[src[0], src[1]] = 1.0
+        un = up.clone()
+        for _ in range(steps):
+            q.qtt_fdtd_step(ctx, c2f, lam2, up, uc, un, None, 0.0)
+            up, uc, un = uc, un, up
+        fields[name] = uc
+    q.qtt_ctx_sync(ctx)
+    rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    out = {
+        "metric": "MPS steps/s, the paper's Sec. 5 run on a synthetic stand-in (256x256, chi=128, 300 steps)",
+        "value": steps / total_s, "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": 0,
+        "ms_per_step": 1e3 * total_s / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "form": args.form, "data": "synthetic (seeded Marmousi-shaped 256x256 section; impulsive initial condition)",
+        "config": {"workload": wl.name, "n": wl.n, "dh_m": wl.dh, "dt_s": wl.dt(c), "chi_max": wl.chi, "eps": wl.eps,
+                   "chi_c": wl.chi_c, "eps_c": wl.eps_c, "order": wl.order, "bc": wl.bc, "source": list(src),
+                   "initial_condition": "u^0 = e_src (strength 1), u^-1 = 0", "graph": bool(args.graph),
+                   "l2": "not flushed: the whole run is timed back to back, first step cold"},
+        "ranks_end": ranks, "c2_model_rel_l2": rel(c2m, c2),
+        "field_rel_l2_vs_dense_fdtd": {k: rel(mps, v) for k, v in fields.items()},
+        "step_ms_curve": [round(x, 3) for x in step_ms[::10]],
+        "step_ms_first_last": [round(step_ms[0], 3), round(step_ms[-1], 3)],
+        "clocks": clk.summary(),
+    }
+    if args.png:
+        write_png_pair(args.png, fields["compressed_c2"].cpu().numpy(), mps.cpu().numpy())
+        out["png"] = args.png
+    return out
+
+
+def run_variants(args):
+    """Boundary-condition and site-order variants as benchmarks: the
+    256x256 layered workload (chi = 64, eps = 1e-7) with PERIODIC or ZERO
+    (Eq. 11 as printed) boundaries and INTERLEAVED or SEQUENTIAL (Eq. 14-15)
+    site order, each from its own mid-run state (the dense Eq. 2 run with the
+    same boundary to step 500, compressed); steps/s, ranks, the MPO bonds and
+    the error against the dense Eq. 2 run after err_steps steps."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    res = {}
+    mid = 500
+    for order in ("interleaved", "sequential"):
+        for bc in ("periodic", "zero"):
+            wl = W.variant(1, order, bc)
+            c = wl.velocity()
+            lam2 = wl.lambda2(c)
+            N = wl.N
+            amps = wl.source_amplitudes(c, mid + args.warmup + args.steps + 2)
+            src = wl.sources[0]
+            stream = torch.cuda.Stream()
+            ctx = q.qtt_ctx_create(n=wl.n, order=order, bc=bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                                   eps_c=wl.eps_c, prec=args.form, stream=stream)
+            with torch.cuda.stream(stream):
+                c_dev = torch.as_tensor(c, device="cuda")
+                C = q.qtt_velocity_mps(ctx, c_dev)
+                L = q.qtt_laplacian_mpo(ctx)
+                c2m = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+                q.qtt_to_dense(C, c2m)
+                up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+                uc, un = up.clone(), up.clone()
+                for k in range(mid):
+                    q.qtt_fdtd_step(ctx, c2m, lam2, up, uc, un, src, float(amps[k]))
+                    up, uc, un = uc, un, up
+                prev, cur = q.qtt_mps_from_dense(ctx, up), q.qtt_mps_from_dense(ctx, uc)
+            step = q.qtt_step_graph if args.graph else q.qtt_step
+            k = mid
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    step(L, C, lam2, prev, cur, src, float(amps[k]))
+                    q.qtt_fdtd_step(ctx, c2m, lam2, up, uc, un, src, float(amps[k]))
+                    up, uc, un = uc, un, up
+                    k += 1
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                for i in range(args.steps):
+                    evs[i][0].record(stream)
+                    step(L, C, lam2, prev, cur, src, float(amps[k]))
+                    evs[i][1].record(stream)
+                    q.qtt_fdtd_step(ctx, c2m, lam2, up, uc, un, src, float(amps[k]))
+                    up, uc, un = uc, un, up
+                    k += 1
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            mps = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+            q.qtt_to_dense(cur, mps)
+            q.qtt_ctx_sync(ctx)
+            rk = q.qtt_mps_ranks(cur)
+            res[f"{order}/{bc}"] = {
+                "ms_per_step": round(ms, 3), "steps_per_s": 1e3 / ms, "ranks": rk, "max_rank": max(rk),
+                "sum_rank": sum(rk), "mpo_bonds": q.qtt_mpo_bonds(L), "c2_ranks": q.qtt_mps_ranks(C),
+                "field_rel_l2_vs_dense_fdtd": float(torch.linalg.norm(mps - uc) / torch.linalg.norm(uc))}
+    base = res["interleaved/periodic"]["ms_per_step"]
+    return {"metric": "MPS steps/s per boundary condition and site order (256x256 layered, chi=64)",
+            "value": 1e3 / base, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "form": args.form, "data": "synthetic (seeded layered section; Ricker source)",
+            "config": {"workload": "qtt256_layered variants", "state": f"mid-run (step {mid}) of each variant",
+                       "graph": bool(args.graph), "l2": "not flushed"},
+            "variants": res}
+
+
+def run_fused(args):
+    """The fused step (Eq. 7's operator A = 2I + lambda^2 C^2 L applied by one
+    zip-up, qtt_step_fused) against the two-zip-up step (qtt_step) on the same
+    mid-run state: steps/s of each, and after err_steps steps the error of
+    each against the FP64 two-zip-up step and against the dense Eq. 2 run."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    wl = W.config(args.fused_cfg)
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    N = wl.N
+    mid = wl.steps // 2
+    nst = args.err_steps
+    amps = wl.source_amplitudes(c, mid + args.warmup + nst + 2)
+    src = wl.sources[0]
+    out, fields = {}, {}
+    zm = args.fused_chi_zip
+    for form, fused, zmul in (("fp64", False, 1), ("fp64", True, 1), ("fp64", True, zm), (args.form, False, 1),
+                              (args.form, True, zm)):
+        key = f"{form}/{'fused' if fused else 'two_zipups'}/chi_zip={zmul}chi"
+        if key in out:
+            continue
+        stream = torch.cuda.Stream()
+        ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                               eps_c=wl.eps_c, prec=form, stream=stream, chi_zip=zmul * wl.chi)
+        C, L, prev, cur = _setup_gpu_state(q, wl, ctx, c, amps, stream, mid)
+        A = q.qtt_a_operator_mpo(L, C, lam2) if fused else None
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for kk in range(nst):
+                if fused:
+                    q.qtt_step_fused(A, prev, cur, src, float(amps[mid + kk]))
+                else:
+                    q.qtt_step(L, C, lam2, prev, cur, src, float(amps[mid + kk]))
+                ev[kk + 1].record(stream)
+        q.qtt_ctx_sync(ctx)
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(nst)]
+        dense = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        q.qtt_to_dense(cur, dense)
+        q.qtt_ctx_sync(ctx)
+        fields[key] = dense.cpu().numpy()
+        out[key] = {"ms_per_step": round(float(np.median(t)), 3), "steps_per_s": 1e3 / float(np.median(t)),
+                    "ranks_end": q.qtt_mps_ranks(cur), "mpo_max_bond": max(q.qtt_mpo_bonds(A if fused else L))}
+        del A, C, L, prev, cur, ctx
+    ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, prec="fp64")
+    c2 = torch.as_tensor(c * c, device="cuda")
+    up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    uc, un = up.clone(), up.clone()
+    for kk in range(mid + nst):
+        q.qtt_fdtd_step(ctx, c2, lam2, up, uc, un, src, float(amps[kk]))
+        up, uc, un = uc, un, up
+    q.qtt_ctx_sync(ctx)
+    fd = uc.cpu().numpy()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    ref = fields["fp64/two_zipups/chi_zip=1chi"]
+    for key in out:
+        out[key]["field_rel_l2_vs_fp64_two_zipups"] = rel(fields[key], ref)
+        out[key]["field_rel_l2_vs_dense_fdtd"] = rel(fields[key], fd)
+    return {"metric": "MPS steps/s, fused Eq. 7 operator (one zip-up) vs two zip-ups", "unit": "steps/s",
+            "value": out[f"{args.form}/fused/chi_zip={zm}chi"]["steps_per_s"], "n_gpus": 1, "steps": nst, "warmup": 0,
+            "higher_is_better": True, "form": args.form,
+            "data": "synthetic (seeded velocity section; Ricker source)",
+            "config": {"workload": wl.name, "n": wl.n, "chi_max": wl.chi, "eps": wl.eps, "chi_c": wl.chi_c,
+                       "state": f"mid-run (step {mid}), dense Eq. 2 compressed by the library",
+                       "timing": "launched steps (no graph), median of err_steps, no L2 flush"},
+            "steps_compared": out}
+
+
+def run_3d(args):
+    """The 3D extension (64^3 layered block, 3n = 18 sites, the 7-point
+    Laplacian MPO, chi = 64, eps = 1e-6, Ricker source at (32, 32, 2)): MPS
+    steps/s from a mid-run state (the dense 7-point run on the GPU to step
+    300, compressed by the library), in the chosen form and in FP64, and the
+    error of both after err_steps steps against the FP64 MPS and the dense
+    run."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    wl = W.qtt3d_run(6)
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    N = wl.N
+    mid = wl.steps // 2
+    nst = args.err_steps
+    amps = wl.source_amplitudes(c, mid + args.warmup + args.steps + nst + 2)
+    src = wl.sources[0]
+    out, fields = {}, {}
+    for form in ("fp64", args.form):
+        if form in out:
+            continue
+        stream = torch.cuda.Stream()
+        ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                               eps_c=wl.eps_c, prec=form, stream=stream, dims=3)
+        with torch.cuda.stream(stream):
+            c_dev = torch.as_tensor(c, device="cuda")
+            C = q.qtt_velocity_mps(ctx, c_dev)
+            L = q.qtt_laplacian_mpo(ctx)
+            c2 = c_dev * c_dev
+            up = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+            uc, un = up.clone(), up.clone()
+            for k in range(mid):
+                q.qtt_fdtd_step_3d(ctx, c2, lam2, up, uc, un, src, float(amps[k]))
+                up, uc, un = uc, un, up
+            prev, cur = q.qtt_mps_from_dense(ctx, up), q.qtt_mps_from_dense(ctx, uc)
+        step = q.qtt_step_graph if args.graph else q.qtt_step
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for kk in range(nst):
+                step(L, C, lam2, prev, cur, src, float(amps[mid + kk]))
+                ev[kk + 1].record(stream)
+                q.qtt_fdtd_step_3d(ctx, c2, lam2, up, uc, un, src, float(amps[mid + kk]))
+                up, uc, un = uc, un, up
+        q.qtt_ctx_sync(ctx)
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(1, nst)]  # the first step captures the graph
+        dense = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+        q.qtt_to_dense(cur, dense)
+        q.qtt_ctx_sync(ctx)
+        fields[form] = dense.cpu().numpy()
+        fields["fdtd"] = uc.cpu().numpy()
+        out[form] = {"ms_per_step": round(float(np.median(t)), 3), "steps_per_s": 1e3 / float(np.median(t)),
+                     "ranks_end": q.qtt_mps_ranks(cur), "c2_ranks": q.qtt_mps_ranks(C),
+                     "mpo_bonds": q.qtt_mpo_bonds(L)}
+        del C, L, prev, cur, ctx
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    for form in out:
+        out[form]["field_rel_l2_vs_fp64_mps"] = rel(fields[form], fields["fp64"])
+        out[form]["field_rel_l2_vs_dense_fdtd"] = rel(fields[form], fields["fdtd"])
+    return {"metric": "MPS steps/s, 3D extension (64^3, 18 sites, 7-point Laplacian, chi=64)", "unit": "steps/s",
+            "value": out[args.form]["steps_per_s"], "n_gpus": 1, "steps": nst - 1, "warmup": 1,
+            "higher_is_better": True, "form": args.form, "data": "synthetic (seeded layered 3D block; Ricker source)",
+            "config": {"workload": wl.name, "n": wl.n, "grid": f"{N}^3", "chi_max": wl.chi, "eps": wl.eps,
+                       "chi_c": wl.chi_c, "order": wl.order, "bc": wl.bc, "source": list(src),
+                       "state": f"mid-run (step {mid} of {wl.steps}), dense 7-point run compressed by the library",
+                       "graph": bool(args.graph), "timing": "median step, CUDA events, no L2 flush"},
+            "forms": out}
+
+
+def run_learned(args):
+    """The learned rounding against plain rounding on the 2048x2048 section
+    (n = 11, chi = 256, eps = 1e-5).  Training data: the plain solver's round
+    spectra (qtt_step_features) and next-step ranks logged over teacher-free
+    steps from mid-run states of the 256x256 layered section, the 1024x1024
+    section and the 512x512 layered section at chi = 256; the network (40 ->
+    128 -> 128 -> 1) is trained on the GPU by the library (mean squared error,
+    Adam).  Then the same mid-run state of the 2048x2048 section is advanced
+    err_steps steps with plain rounding and with the learned rounding: the
+    logged Jacobi SVD work, the step times and the field difference between
+    the two (and against the dense Eq. 2 run) are reported."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    form = args.form
+    feats, labels, sources = [], [], []
+    X = None
+    for idx, nsteps, chi_o in ((1, 40, None), (2, 12, None), (3, 12, 256)):
+        wl = W.config(idx)
+        chi = chi_o or wl.chi
+        c = wl.velocity()
+        lam2 = wl.lambda2(c)
+        mid = wl.steps // 2
+        amps = wl.source_amplitudes(c, mid + nsteps + 2)
+        stream = torch.cuda.Stream()
+        ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=chi, eps=wl.eps, chi_c=wl.chi_c,
+                               eps_c=wl.eps_c, prec=form, stream=stream, learned=True)
+        C, L, prev, cur = _setup_gpu_state(q, wl, ctx, c, amps, stream, mid)
+        X = torch.zeros((ctx.d - 1, 40), dtype=torch.float32, device="cuda")
+        f_run, r_run = [], []
+        with torch.cuda.stream(stream):
+            for k in range(nsteps):
+                q.qtt_step(L, C, lam2, prev, cur, wl.sources[0], float(amps[mid + k]))
+                q.qtt_step_features(cur, X)
+                q.qtt_ctx_sync(ctx)
+                f_run.append(X.cpu().numpy().copy())
+                r_run.append(q.qtt_mps_ranks(cur))
+        feats.append(np.concatenate(f_run[:-1]))
+        labels.append(np.concatenate([np.array(r[1:-1], dtype=np.float32) / chi for r in r_run[1:]]))
+        sources.append(f"{wl.name} chi={chi}: {nsteps} steps from step {mid}")
+        del C, L, prev, cur, ctx
+    Xs, ys = np.concatenate(feats), np.concatenate(labels)
+    mlp = q.qtt_mlp_create(W.mlp_params(7), len(Xs))
+    Xg = torch.as_tensor(Xs, device="cuda")
+    yg = torch.as_tensor(ys, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    q.qtt_mlp_grad(mlp, Xg, yg, loss)
+    loss0 = float(loss.item())
+    for _ in range(800):
+        q.qtt_mlp_grad(mlp, Xg, yg, loss)
+        q.qtt_mlp_adam_step(mlp, 2e-3)
+    loss1 = float(loss.item())
+    # evaluation on the 2048x2048 section
+    wl = W.config(4)
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    mid = wl.steps // 2
+    nst = args.err_steps
+    amps = wl.source_amplitudes(c, mid + nst + 2)
+    N = wl.N
+    G = torch.as_tensor(W.gaussian_sketch(11, 1024, 512), device="cuda")
+    res, fields = {}, {}
+    for mode in ("plain", "learned"):
+        stream = torch.cuda.Stream()
+        ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                               eps_c=wl.eps_c, prec=form, stream=stream, learned=True)
+        C, L, prev, cur = _setup_gpu_state(q, wl, ctx, c, amps, stream, mid)
+        if mode == "learned":
+            q.qtt_set_rank_model(ctx, mlp, G)
+        q.qtt_profile_start(ctx, timing=False, log_svd=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for k in range(nst):
+                q.qtt_step(L, C, lam2, prev, cur, wl.sources[0], float(amps[mid + k]))
+                ev[k + 1].record(stream)
+        q.qtt_ctx_sync(ctx)
+        prof = q.qtt_profile_read(ctx)
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(nst)]
+        dense = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        q.qtt_to_dense(cur, dense)
+        q.qtt_ctx_sync(ctx)
+        fields[mode] = dense.cpu().numpy()
+        att, acc = q.qtt_learned_stats(ctx)
+        res[mode] = {"ms_per_step": round(float(np.mean(t)), 2), "steps_per_s": 1e3 / float(np.mean(t)),
+                     "svd_work_flop": prof["svd_flops"], "jacobi_launches": prof["svd_logged"],
+                     "range_finder_attempts": att, "range_finder_accepts": acc, "ranks_end": q.qtt_mps_ranks(cur)}
+        q.qtt_set_rank_model(ctx, None, None)
+        del C, L, prev, cur, ctx
+    ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, prec="fp64")
+    c2 = torch.as_tensor(c * c, device="cuda")
+    up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    uc, un = up.clone(), up.clone()
+    for kk in range(mid + nst):
+        q.qtt_fdtd_step(ctx, c2, lam2, up, uc, un, wl.sources[0], float(amps[kk]))
+        up, uc, un = uc, un, up
+    q.qtt_ctx_sync(ctx)
+    fd = uc.cpu().numpy()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return {"metric": "learned vs plain rounding, 2048x2048 section (chi=256, eps=1e-5): SVD work and steps/s",
+            "unit": "ratio", "value": res["learned"]["svd_work_flop"] / max(res["plain"]["svd_work_flop"], 1.0),
+            "higher_is_better": False, "n_gpus": 1, "steps": nst, "form": form,
+            "data": "synthetic (seeded Marmousi-shaped sections; Ricker sources)",
+            "config": {"workload": wl.name, "n": wl.n, "chi_max": wl.chi, "eps": wl.eps,
+                       "state": f"mid-run (step {mid} of {wl.steps})", "training": sources,
+                       "training_samples": int(len(Xs)), "loss_first_last": [loss0, loss1],
+                       "timing": "launched steps (the learned form reads each accept flag on the host)"},
+            "plain": res["plain"], "learned": res["learned"],
+            "field_rel_l2_learned_vs_plain": rel(fields["learned"], fields["plain"]),
+            "field_rel_l2_vs_dense_fdtd": {m: rel(fields[m], fd) for m in fields},
+            "speedup_learned_vs_plain": res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"]}
+
+
 def compare_forms(q, wl, c, amps, args):
     """The plain FP64 form timed on the same mid-run state, and the error of
     both forms after args.err_steps steps: against each other, and against
@@ -428,8 +919,9 @@ def compare_forms(q, wl, c, amps, args):
     rx = torch.as_tensor(np.array([r[0] for r in wl.receivers]), device="cuda")
     rz = torch.as_tensor(np.array([r[1] for r in wl.receivers]), device="cuda")
     out = {}
-    fields, traces = {}, {}
-    for form in ("fp64", args.form):
+    fields, traces, times = {}, {}, {}
+    extra = [f for f in (args.compare_forms.split(",") if args.compare_forms else []) if f]
+    for form in ["fp64", args.form] + extra:
         if form in fields:
             continue
         stream = torch.cuda.Stream()
@@ -445,8 +937,9 @@ def compare_forms(q, wl, c, amps, args):
                 ev[kk + 1].record(stream)
                 q.qtt_sample(cur, rx, rz, tr[kk])
         q.qtt_ctx_sync(ctx)
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.err_steps)]
+        times[form] = float(np.mean(t))
         if form == "fp64":
-            t = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.err_steps)]
             out = {"ms_per_step": float(np.mean(t)), "value": 1000.0 / float(np.mean(t)), "unit": UNIT,
                    "steps": args.err_steps, "note": "same state and steps as the error check, no L2 flush"}
         dense = torch.zeros((N, N), dtype=torch.float64, device="cuda")
@@ -473,47 +966,34 @@ def compare_forms(q, wl, c, amps, args):
            "field_rel_l2_vs_dense_fdtd": {f: rel(fields[f], fd) for f in fields},
            "threshold": 1e-3}
     err["eligible"] = err["field_rel_l2_vs_fp64_mps"] <= 1e-3 and err["trace_rel_l2_vs_fp64_mps"] <= 1e-3
+    err["forms"] = {}
+    for f in fields:
+        fe, te = rel(fields[f], fields["fp64"]), rel(traces[f], traces["fp64"])
+        err["forms"][f] = {"ms_per_step_launched": round(times[f], 3), "steps_per_s_launched": 1000.0 / times[f],
+                           "field_rel_l2_vs_fp64_mps": fe, "trace_rel_l2_vs_fp64_mps": te,
+                           "field_rel_l2_vs_dense_fdtd": rel(fields[f], fd), "eligible": fe <= 1e-3 and te <= 1e-3}
+    err["forms_note"] = ("every form from the same mid-run state, err_steps launched steps (no graph, no L2 flush); "
+                         "errors against the FP64 MPS after those steps")
     return out, err
 
 
-def oracle_baseline(seconds: float, mid_run: int = 600):
-    """The FP64 oracle on the host cores: a bounded sample of the same
-    workload (its own FDTD to a state with saturated ranks, then timed MPS
-    steps until ~`seconds` of stepping)."""
-    from oracle import qtt_oracle as O
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:  # pragma: no cover
-        cores = os.cpu_count() or 1
-    wl = W.config(WORKLOAD_IDX)
-    n = wl.n
-    c = wl.velocity()
-    c2 = c * c
-    lam2 = wl.lambda2(c)
-    amps = wl.source_amplitudes(c, mid_run + 64)
-    up = np.zeros((wl.N, wl.N))
-    uc = np.zeros((wl.N, wl.N))
-    for k in range(mid_run):
-        up, uc = uc, O.fdtd_step(up, uc, c2, lam2, wl.bc, wl.sources[0], float(amps[k]))
-    Co = O.velocity_mps(c, n, wl.order, wl.eps_c, wl.chi_c)
-    Lo = O.laplacian_mpo(n, wl.order, wl.bc)
-    prev = O.state_from_dense(up, n, wl.order, wl.eps, wl.chi)
-    cur = O.state_from_dense(uc, n, wl.order, wl.eps, wl.chi)
-    t0 = time.perf_counter()
-    steps = 0
-    k = mid_run
-    while True:
-        prev, cur = cur, O.mps_step(Lo, Co, lam2, prev, cur, wl.eps, wl.chi, wl.sources[0], float(amps[k]), n,
-                                    wl.order)
-        steps += 1
-        k += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} oracle steps of {wl.name} from its own FDTD state at step {mid_run} "
-                      f"(ranks {max(O.mps_ranks(cur))} max), {dt:.1f} s"}
+def oracle_baseline(steps: int = 10, warmup: int = 3) -> dict:
+    """The FP64 oracle on the host cores, in a process of its own (the
+    reference arm of this script: `bench.py --impl reference`), so that no
+    thread of the GPU process competes with its BLAS threads: `steps` timed
+    oracle steps after `warmup`, from the same mid-run state as the GPU arm."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(steps),
+           "--warmup", str(warmup)]
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    if out.returncode != 0 or not line:
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                "sample": f"reference arm failed (rc {out.returncode}): {out.stderr[-300:]}"}
+    ref = json.loads(line[-1])
+    cb = dict(ref["cpu_baseline"])
+    cb["same_config"] = True
+    return cb
 
 
 def run_reference(args, rank, world):
@@ -524,7 +1004,7 @@ def run_reference(args, rank, world):
     n = wl.n
     c = wl.velocity()
     lam2 = wl.lambda2(c)
-    mid = 600
+    mid = MID_RUN
     amps = wl.source_amplitudes(c, mid + args.warmup + args.steps + 2)
     up = np.zeros((wl.N, wl.N))
     uc = np.zeros((wl.N, wl.N))
@@ -555,10 +1035,12 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "n": n, "chi_max": wl.chi, "eps": wl.eps, "form": "fp64 oracle (numpy)",
-                   "state": f"oracle FDTD at step {mid}"},
+        "config": workload_config(wl, mid),
+        "form": "fp64 oracle (numpy, LAPACK svd/qr)",
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} timed oracle steps after {args.warmup} warm-up, {dt:.1f} s"},
+                         "sample": f"{args.steps} timed oracle steps after {args.warmup} warm-up from the oracle's "
+                                   f"own dense Eq. 2 state at step {mid} (ranks {max(O.mps_ranks(cur))} max), "
+                                   f"{dt:.1f} s"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -570,15 +1052,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32"],
-                    help="fp32: the chosen form (FP32 contractions/QR, FP64-accurate SVDs); fp64: the plain form")
+    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32", "tf32x3", "tf32", "bf16"],
+                    help="fp32: the chosen form (FP32 contractions/QR, FP64-accurate SVDs); fp64: the plain form; "
+                         "tf32x3 / tf32 / bf16: the FP32 form with tensor-core contractions")
     ap.add_argument("--compare", type=int, default=1, help="also time the plain FP64 form and measure errors")
     ap.add_argument("--err-steps", type=int, default=20)
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--compare-forms", default="tf32x3,tf32,bf16",
+                    help="further forms whose step time and error after --err-steps are reported")
+    ap.add_argument("--cpu-steps", type=int, default=10, help="timed oracle steps of the cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1, help="1: autotune launch shapes before timing (qtt_autotune)")
     ap.add_argument("--graph", type=int, default=1, help="1: replay each step from a CUDA graph (qtt_step_graph); 0: launch the kernels")
-    ap.add_argument("--workload", default="qtt1024_marmousi", choices=["qtt1024_marmousi", "qtt512_64shots"],
-                    help="qtt512_64shots: the batched multi-shot step instead of the headline workload")
+    ap.add_argument("--workload", default="qtt1024_marmousi",
+                    choices=["qtt1024_marmousi", "qtt512_64shots", "paper256", "variants", "fused", "qtt3d",
+                             "learned"],
+                    help="qtt512_64shots: the batched multi-shot step; paper256: the paper's Sec. 5 run on the "
+                         "synthetic stand-in; variants: boundary conditions and site orders")
+    ap.add_argument("--fused-cfg", type=int, default=1, help="fused: the configuration index (1: 256x256 layered)")
+    ap.add_argument("--fused-chi-zip", type=int, default=4, help="fused: the zip-up bond cap as a multiple of chi")
+    ap.add_argument("--png", default=None, help="paper256: write the FDTD | MPS field pair to this PNG file")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -590,9 +1082,11 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.workload == "qtt512_64shots":
+    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned"):
         if rank == 0:
-            print(json.dumps(run_shots(args)), flush=True)
+            fn = {"qtt512_64shots": run_shots, "paper256": run_paper, "variants": run_variants,
+                  "fused": run_fused, "qtt3d": run_3d, "learned": run_learned}[args.workload]
+            print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:
         import torch
@@ -602,7 +1096,7 @@ def main():
     res, _keep = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            res["cpu_baseline"] = oracle_baseline(args.cpu_seconds)
+            res["cpu_baseline"] = oracle_baseline(args.cpu_steps)
         else:
             res["cpu_baseline"] = None
         print(json.dumps(res), flush=True)

@@ -54,7 +54,7 @@ typedef enum {
 
 typedef enum { QTT_ORDER_SEQUENTIAL = 0, QTT_ORDER_INTERLEAVED = 1 } qtt_order;
 typedef enum { QTT_BC_PERIODIC = 0, QTT_BC_ZERO = 1 } qtt_bc;
-typedef enum { QTT_FP64 = 0, QTT_TF32 = 1, QTT_BF16 = 2, QTT_FP32 = 3 } qtt_precision;
+typedef enum { QTT_FP64 = 0, QTT_TF32 = 1, QTT_BF16 = 2, QTT_FP32 = 3, QTT_TF32X3 = 4 } qtt_precision;
 
 /* Solver parameters.  n: bits per axis (1..14).  order: qtt_order.  bc:
  * qtt_bc; PERIODIC is the cyclic shift |x> -> |(x+1) mod 2^n> of Sec. 3.1 and
@@ -63,11 +63,23 @@ typedef enum { QTT_FP64 = 0, QTT_TF32 = 1, QTT_BF16 = 2, QTT_FP32 = 3 } qtt_prec
  * contractions (qtt_precision): QTT_FP64 is the plain form; QTT_FP32 runs
  * the contractions and QR updates in FP32 and the truncation SVD of each
  * bond factor as an FP32 Jacobi refined to FP64 accuracy in FP64 (the
- * singular values, the rank decision and the discarded weight are FP64).  chi_max, eps:
+ * singular values, the rank decision and the discarded weight are FP64).
+ * QTT_TF32, QTT_TF32X3 and QTT_BF16 are QTT_FP32 with the core contractions
+ * (zip-up site contractions, the Hadamard contraction with c^2, the
+ * absorption of R and U S factors; Sec. 4.3) on the tensor cores (tcgen05,
+ * FP32 accumulation in tensor memory): TF32 operands, TF32 operands split
+ * x = hi + lo with the products hi*hi + hi*lo + lo*hi (about FP32
+ * accuracy), or BF16 operands.  chi_max, eps:
  * truncation of the state (Sec. 4.3).  chi_zip, eps_zip: truncation inside
  * the two zip-up applications (0 = use chi_max / eps).  chi_c, eps_c:
  * truncation of the c^2 MPS (the paper does not say; 0 = chi_max / 1e-8).
- * use_learned_rank: 1 enables the learned rounding (qtt_set_rank_model). */
+ * use_learned_rank: 1 enables the learned rounding (qtt_set_rank_model).
+ * dims: 2 (or 0) for the 2D scheme of Eq. 2; 3 for its 3D extension (the
+ * paper's discussion section): an N^3 grid u[(x N + y) N + z] on d = 3n
+ * sites (n <= 9), SEQUENTIAL = x, y, z registers one after another,
+ * INTERLEAVED = x_0, y_0, z_0, x_1, ..., the 7-point Laplacian; every call
+ * that takes a grid point then takes three coordinates (src_ixiz of the
+ * step calls holds {ix, iy, iz}; the *_3d calls below). */
 typedef struct {
   int n;
   int order;
@@ -80,6 +92,7 @@ typedef struct {
   int chi_c;
   double eps_c;
   int use_learned_rank;
+  int dims;
 } qtt_params;
 
 typedef struct qtt_ctx qtt_ctx;
@@ -98,6 +111,18 @@ const char* qtt_last_error(void);
 /* Wait for the context stream and return (then clear) the device status. */
 qtt_status qtt_ctx_sync(qtt_ctx* ctx);
 
+/* Failure-detection limits of the context (the bounded waits and sweep
+ * limit behind QTT_ETIMEOUT and QTT_ENOCONV).  wait_limit_s: how long a
+ * kernel waits on another CTA of its launch (a grid barrier, a published
+ * reflector or Jacobi round) before it records QTT_ETIMEOUT and returns;
+ * <= 0 restores the default of 2 s.  max_sweeps: sweeps of the FP64 Jacobi
+ * SVD before it records QTT_ENOCONV; <= 0 restores the default of 100.  A
+ * kernel that gave up leaves its outputs undefined; the next synchronising
+ * call reports the status and resets the device status word, after which the
+ * context is usable again.  Captured step graphs are dropped (they are
+ * captured again on the next qtt_step_graph). */
+qtt_status qtt_set_limits(qtt_ctx* ctx, double wait_limit_s, int max_sweeps);
+
 /* ------------------------------------------------------------------ states */
 
 /* Rank-1 MPS of the zero field (the zero initial condition). */
@@ -106,8 +131,8 @@ qtt_status qtt_mps_create_zero(qtt_ctx* ctx, qtt_mps** out);
 /* MPS of a dense field: sequential truncated SVDs (TT-SVD, Eq. 8) with
  * (chi_max, eps), then the compression of Sec. 4.3 (QR sweep, SVD sweep),
  * so that cores 1..d-1 are right-orthonormal as qtt_step expects.  grid: N*N
- * doubles u[x*N+z], device memory if on_device else host memory (copied;
- * the call waits for it).  Synchronises. */
+ * doubles u[x*N+z] (3D: N^3, u[(x*N+y)*N+z]), device memory if on_device
+ * else host memory (copied; the call waits for it).  Synchronises. */
 qtt_status qtt_mps_from_dense(qtt_ctx* ctx, const double* grid, int on_device, qtt_mps** out);
 
 /* MPS from explicit cores.  ranks: d+1 host ints (ranks[0] = ranks[d] = 1,
@@ -127,13 +152,14 @@ void qtt_mps_destroy(qtt_mps* psi);
 
 /* MPS of the squared velocity c^2(x,z) (the diagonal operator C^2 of Eq. 4,
  * used as a diagonal MPO in Sec. 4.3), by TT-SVD (Eq. 8) with
- * (chi_c, eps_c).  c_grid: N*N velocities (m/s, > 0), device if on_device
- * else host.  Synchronises (the c^2 ranks are fixed for the run). */
+ * (chi_c, eps_c).  c_grid: N*N velocities (m/s, > 0; N^3 in 3D), device if
+ * on_device else host.  Synchronises (the c^2 ranks are fixed for the run). */
 qtt_status qtt_velocity_mps(qtt_ctx* ctx, const double* c_grid, int on_device, qtt_mps** c2_out);
 
 /* Laplacian MPO S_x^+ + S_x^- + S_z^+ + S_z^- - 4I (Eq. 16) built from the
  * carry tensors of Eq. 9-13 as one five-state carry automaton, for the
- * context's order and boundary condition.  Built on the host, copied once. */
+ * context's order and boundary condition (3D: the 7-point operator with the
+ * y shifts, a seven-state automaton).  Built on the host, copied once. */
 qtt_status qtt_laplacian_mpo(qtt_ctx* ctx, qtt_mpo** out);
 /* Bond dimensions w_0..w_d of an MPO (d+1 host ints). */
 qtt_status qtt_mpo_bonds(const qtt_mpo* L, int* bonds_out);
@@ -151,12 +177,14 @@ qtt_status qtt_mps_load(qtt_ctx* ctx, const char* path, qtt_mps** out);
 /* psi <- round(psi + amp * e_(ix,iz)): a rank-1 product-state add (the
  * impulsive source of Sec. 5) followed by the Sec. 4.3 compression. */
 qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, double amp);
+/* The same at (ix, iy, iz) of a 3D context. */
+qtt_status qtt_inject_source_3d(qtt_ctx* ctx, qtt_mps* psi, long ix, long iy, long iz, double amp);
 
 /* One time step of Eq. 17.  On entry psi_prev = u^{k-1}, psi_cur = u^k; on
  * return psi_prev = u^k and psi_cur = u^{k+1} (the handles exchange their
  * buffers; nothing is reallocated).  lambda2 = (dt/dh)^2 (Eq. 2).
- * src_ixiz: NULL for no source, else a host pair {ix, iz} where src_amp is
- * added to u^{k+1} as a rank-1 product state.  psi_cur must be right-
+ * src_ixiz: NULL for no source, else a host pair {ix, iz} ({ix, iy, iz} in
+ * 3D) where src_amp is added to u^{k+1} as a rank-1 product state.  psi_cur must be right-
  * orthonormal in cores 1..d-1 (as every state this library returns is) for
  * the zip-up truncation to measure the right norm. */
 qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2,
@@ -173,6 +201,46 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
  * timing is on (QTT_EINVAL).  Results are those of qtt_step. */
 qtt_status qtt_step_graph(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps* psi_prev,
                           qtt_mps* psi_cur, const long* src_ixiz, double src_amp);
+
+/* Autotuner of the step's launch shapes.  Runs one dry-run step (no source)
+ * on copies of (psi_prev, psi_cur), recording every contraction GEMM (the
+ * core contractions of Sec. 4.3 and the FP64 products of the SVD
+ * refinement) and every Householder QR; groups them by bucket (kind and
+ * operand precision, the host-side size bounds, batch count); times every
+ * candidate on all launches of a bucket with their own arguments and
+ * device-side sizes, reps times after a warm-up (CUDA events on the context
+ * stream); and keeps the fastest for later steps of the context: the output
+ * tile (16 or 32) of the SIMT GEMMs, the tile width (64, 128 or 256 columns)
+ * of the tensor-core contractions, the threads per CTA (256 or 1024) of the
+ * QR.  cache_path (may be NULL): a JSON file; if it holds the choices for
+ * this device, form and shape (a header line), they are loaded instead of
+ * measured, else the measured choices are written there.  *entries_out
+ * (may be NULL): the number of buckets tuned.  The states are not changed.
+ * Captured step graphs are dropped.  Synchronises.  The paper has no
+ * counterpart; the choices change no result beyond rounding. */
+qtt_status qtt_autotune(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, const qtt_mps* psi_prev,
+                        const qtt_mps* psi_cur, const char* cache_path, int reps, int* entries_out);
+
+/* The transition operator of Eq. 7, A = 2I + lambda^2 C^2 L, as one MPO:
+ * the product of the diagonal MPO of the c^2 MPS (Sec. 4.3) and the
+ * Laplacian MPO (Eq. 16) plus twice the identity, bond r_c w + 1 (r_c the
+ * c^2 ranks, w the Laplacian bonds).  The norm nu of the last c^2 core is
+ * carried by the coefficient of the product term (lambda^2 nu on the first
+ * core, the last c^2 core divided by nu), so that both terms are of order one
+ * at every bond.  Built on the host (the c^2 cores are copied back; the call
+ * synchronises), copied to the device once; released by qtt_mpo_destroy. */
+qtt_status qtt_a_operator_mpo(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mpo** out);
+
+/* One time step of Eq. 7 with A applied as one operator (the fused variant
+ * of qtt_step): phi = A psi^k by one zip-up (sites 1 -> d, truncated with
+ * chi_zip / eps_zip), theta = phi - psi^{k-1} [+ src_amp e_src], psi^{k+1} =
+ * round(theta) (Sec. 4.3).  In exact arithmetic the step of qtt_step; one
+ * truncated zip-up instead of two.  A: from qtt_a_operator_mpo (any MPO is
+ * accepted: the step then advances psi^{k+1} = round(A psi^k - psi^{k-1})).
+ * Handles rotate as in qtt_step.  The workspace is sized for A's bonds (a
+ * context alternating this and qtt_step regrows it). */
+qtt_status qtt_step_fused(qtt_ctx* ctx, const qtt_mpo* A, qtt_mps* psi_prev, qtt_mps* psi_cur, const long* src_ixiz,
+                          double src_amp);
 
 /* Batched shots.  A batch holds one context per shot (each with its own
  * chi_max and workspace, all on `cuda_stream`) and a pool of min(nshots, 8)
@@ -193,7 +261,8 @@ qtt_ctx* qtt_batch_ctx(qtt_batch* batch, int shot);
 /* L and c2 are shared by all shots (created in any context of the same n,
  * order and boundary condition).  prev, cur: nshots handles each, created in
  * the shots' contexts; they rotate as in qtt_step.  src_ixiz: NULL, or
- * 2*nshots host longs {ix_0, iz_0, ix_1, ...}; src_amp: nshots doubles. */
+ * 2*nshots host longs {ix_0, iz_0, ix_1, ...} (3*nshots in 3D);
+ * src_amp: nshots doubles. */
 qtt_status qtt_step_batched(qtt_batch* batch, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mps** prev,
                             qtt_mps** cur, const long* src_ixiz, const double* src_amp);
 void qtt_batch_destroy(qtt_batch* batch);
@@ -275,7 +344,12 @@ qtt_status qtt_learned_stats(qtt_ctx* ctx, long* attempts, long* accepts);
 qtt_status qtt_sample(qtt_ctx* ctx, const qtt_mps* psi, const long* ix_dev, const long* iz_dev,
                       long count, double* out_dev);
 
-/* Full contraction to the dense grid: out_dev[x*N+z], N*N device doubles. */
+/* Receiver readout of a 3D context: out[p] at (ix[p], iy[p], iz[p]). */
+qtt_status qtt_sample_3d(qtt_ctx* ctx, const qtt_mps* psi, const long* ix_dev, const long* iy_dev,
+                         const long* iz_dev, long count, double* out_dev);
+
+/* Full contraction to the dense grid: out_dev[x*N+z], N*N device doubles
+ * (3D: out_dev[(x*N+y)*N+z], N^3 device doubles). */
 qtt_status qtt_to_dense(qtt_ctx* ctx, const qtt_mps* psi, double* out_dev);
 
 /* ------------------------------------------------------- linear algebra */
@@ -309,6 +383,21 @@ qtt_status qtt_svd_trunc(qtt_ctx* ctx, const double* M_dev, int m, int n, double
 qtt_status qtt_svd_trunc_noalloc(const double* M_dev, int m, int n, double eps, int chi, double* U_dev,
                                  double* S_dev, double* Vt_dev, int* rank_out, void* cuda_stream);
 
+/* One core contraction on its own, the kernel every contraction of a step
+ * uses (the zip-up site contractions, the Hadamard contraction with the c^2
+ * cores and the absorption of R and U S factors into neighbouring cores,
+ * Sec. 4.3): C = alpha op(A) op(B) + beta C on the context stream, with
+ * op(A) m x k, op(B) k x n, all device FP64 row-major: A is m x k (lda) or,
+ * if a_trans, k x m; B is k x n (ldb) or, if b_trans, n x k; C is m x n
+ * (ldc).  kind: 0 FP64, 1 FP32 (SIMT kernels); 2 TF32, 3 3xTF32 (x split
+ * into two TF32 parts, three products), 4 BF16 (tensor cores, tcgen05 with
+ * the FP32 accumulator in tensor memory).  tile_n: columns per CTA of the
+ * tensor-core kinds (64, 128 or 256; 0 = the library's choice).  QTT_EINVAL
+ * for bad sizes or leading dimensions; asynchronous (qtt_ctx_sync reports
+ * device failures). */
+qtt_status qtt_gemm(qtt_ctx* ctx, int kind, int a_trans, int b_trans, int m, int n, int k, const double* A, int lda,
+                    const double* B, int ldb, double* C, int ldc, double alpha, double beta, int tile_n);
+
 /* ------------------------------------------------------------- context */
 
 /* Dense FDTD update of Eq. 2 on the device (the scheme the MPS step
@@ -319,6 +408,12 @@ qtt_status qtt_svd_trunc_noalloc(const double* M_dev, int m, int n, double eps, 
 qtt_status qtt_fdtd_step(qtt_ctx* ctx, const double* c2_dev, double lambda2, const double* u_prev_dev,
                          const double* u_cur_dev, double* u_next_dev, long src_ix, long src_iz,
                          double amp);
+/* The 7-point update of a 3D context (arrays N^3, u[(x*N+y)*N+z]): six face
+ * neighbours, - 6 u_cur, the context's boundary rule; amp at the source
+ * when every coordinate is in range. */
+qtt_status qtt_fdtd_step_3d(qtt_ctx* ctx, const double* c2_dev, double lambda2, const double* u_prev_dev,
+                            const double* u_cur_dev, double* u_next_dev, long src_ix, long src_iy, long src_iz,
+                            double amp);
 
 /* Singular values, kept ranks and discarded weights of the last step, for
  * diagnostics.  discarded: 3*(d-1) host doubles (zip-up L bonds 1..d-1,
@@ -343,16 +438,35 @@ typedef struct {
                                   the two sizes of the rotated problem) */
   long svd_sweeps;             /* Jacobi sweeps over them (the last one finds
                                   no pair to rotate) */
+  double flops[QTT_KCLASSES];  /* algorithmic FLOPs of the launches of each
+                                  class while work logging is on (log_svd),
+                                  counted by the kernels from their device-side
+                                  sizes: 2 M N K per GEMM (batches included),
+                                  2 p k^2 - 2k^3/3 per Householder QR of a
+                                  p x q matrix (k = min(p, q)) and the same again
+                                  for its thin Q; the cluster factorisations
+                                  and the Jacobi sweeps are not counted here
+                                  (svd_flops holds the SVD work) */
 } qtt_profile;
 
 /* Reset the counters of the context.  timing != 0 brackets every launch with
  * CUDA events on the context stream (adds a little host work per launch);
- * log_svd != 0 records the size of up to 65536 Jacobi launches.  Counting
- * launches is always on. */
+ * log_svd != 0 records the size of up to 65536 Jacobi launches and counts
+ * the algorithmic FLOPs per class (qtt_profile.flops).  Counting launches is
+ * always on.  qtt_step_graph refuses to capture while timing or logging is
+ * on. */
 qtt_status qtt_profile_start(qtt_ctx* ctx, int timing, int log_svd);
 
 /* Read the counters (synchronises the stream). */
 qtt_status qtt_profile_read(qtt_ctx* ctx, qtt_profile* out);
+
+/* Measured ALU peak of the current device: kind 0 = FP32 FMA, 1 = FP64 FMA.
+ * Runs an FMA-chain kernel (8 independent chains per thread, 32 warps per
+ * SM) for about 60 ms on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream) and writes 2 x FMAs / elapsed time in TFLOP/s to *tflops.  These
+ * are the roofline peaks of the SIMT kernels (the FP32 Jacobi, the FP64
+ * refinement and Jacobi).  Synchronises; allocates a small device buffer. */
+qtt_status qtt_peak_probe(int kind, double* tflops, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,7 @@ constexpr int BK = 16, NT = 256;
 struct GemmKArgs {
   GemmArgs a;
   long long nb2max;
+  double* flops;  // algorithmic FLOP counter of the launch's class (null: not counting)
 };
 
 // T: arithmetic of the products and the accumulation (double, or float for
@@ -31,6 +32,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmKArgs ka) {
   const long long bz = blockIdx.z;
   const long long b1 = bz / ka.nb2max, b2 = bz % ka.nb2max;
   const long long i0 = (long long)blockIdx.y * TM, j0 = (long long)blockIdx.x * TN;
+  if (ka.flops && bz == 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(ka.flops, 2.0 * (double)M * (double)N * (double)K * (double)dv(a.nb1) * (double)dv(a.nb2));
   if (i0 >= M || j0 >= N || b1 >= dv(a.nb1) || b2 >= dv(a.nb2)) return;
 
   const long long sai = dv(a.sai), sak = dv(a.sak), sbk = dv(a.sbk), sbj = dv(a.sbj);
@@ -97,14 +100,16 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmKArgs ka) {
 
 template <typename T>
 cudaError_t gemm_launch(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max, long long nb2max,
-                        cudaStream_t st) {
+                        cudaStream_t st, int tile) {
   if (Mmax <= 0 || Nmax <= 0 || nb1max <= 0 || nb2max <= 0) return cudaSuccess;
   const long long gz = nb1max * nb2max;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
-  GemmKArgs ka{a, nb2max};
+  GemmKArgs ka{a, nb2max, g_flop_ctr};
   // 32x32 tiles when they already cover the SMs, else 16x16 tiles (4x the CTAs)
   const long long big = ((Nmax + 31) / 32) * ((Mmax + 31) / 32) * gz;
-  if (big >= 148) {
+  if (tile == 0) tile = big >= device_sms() ? 32 : 16;
+  if (tile != 16 && tile != 32) return cudaErrorInvalidValue;
+  if (tile == 32) {
     const long long gx = (Nmax + 31) / 32, gy = (Mmax + 31) / 32;
     if (gx > 2147483647LL || gy > 65535) return cudaErrorInvalidConfiguration;
     gemm_kernel<T, 32, 32><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), NT, 0, st>>>(ka);
@@ -119,13 +124,13 @@ cudaError_t gemm_launch(const GemmArgs& a, long long Mmax, long long Nmax, long 
 }  // namespace
 
 cudaError_t gemm_f64(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max, long long nb2max,
-                     cudaStream_t st) {
-  return gemm_launch<double>(a, Mmax, Nmax, nb1max, nb2max, st);
+                     cudaStream_t st, int tile) {
+  return gemm_launch<double>(a, Mmax, Nmax, nb1max, nb2max, st, tile);
 }
 
 cudaError_t gemm_f32(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max, long long nb2max,
-                     cudaStream_t st) {
-  return gemm_launch<float>(a, Mmax, Nmax, nb1max, nb2max, st);
+                     cudaStream_t st, int tile) {
+  return gemm_launch<float>(a, Mmax, Nmax, nb1max, nb2max, st, tile);
 }
 
 }  // namespace qtt

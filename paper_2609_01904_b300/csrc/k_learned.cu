@@ -209,7 +209,7 @@ __global__ void rf_accept_kernel(const double* sig, const int* nsv_p, const int*
 
 inline int eg(long long total) {
   long long g = (total + 255) / 256;
-  return (int)std::max(1LL, std::min(g, 148LL * 8));
+  return (int)std::max(1LL, std::min(g, device_sms() * 8LL));
 }
 
 }  // namespace

@@ -93,7 +93,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, Dim lda_d, T* W, long long ldw,
                                                 Dim m_d, Dim n_d, T* tau, double* Rout, int r_rowmajor,
                                                 long long ldr, double* Qout, int* kq_out, int* flag,
-                                                DevSync* sync) {
+                                                DevSync* sync, double* flops) {
   __shared__ T red[32];
   __shared__ int s_ok;
   extern __shared__ unsigned char ysh_raw[];
@@ -101,7 +101,16 @@ __global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, D
   const long long m = dv(m_d), n = dv(n_d), lda = dv(lda_d);
   const long long kq = m < n ? m : n;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  if (flops && b == 0 && tid == 0) {  // Householder R: 2 p k^2 - 2k^3/3; thin Q: 2 m k^2 - 2k^3/3
+    const double p = (double)(m > n ? m : n), k = (double)kq;
+    double f = 2.0 * p * k * k - 2.0 * k * k * k / 3.0;
+    if (Qout) f += 2.0 * (double)m * k * k - 2.0 * k * k * k / 3.0;
+    atomicAdd(flops, f);
+  }
 
+  // the rank of R is known from the sizes: written first, so that a launch
+  // that gives up on a wait still leaves its consumers a size in range
+  if (kq_out && b == 0 && tid == 0) *kq_out = (int)kq;
   for (long long c = b; c < n; c += G)
     for (long long i = tid; i < m; i += B) W[c * ldw + i] = T(Ain[c * lda + i]);
   for (long long j = (long long)b * B + tid; j < kq; j += (long long)G * B) flag[j] = 0;
@@ -151,7 +160,6 @@ __global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, D
       else Rout[c * ldr + i] = r;
     }
   }
-  if (kq_out && b == 0 && tid == 0) *kq_out = (int)kq;
   if (!Qout || kq == 0) return;
 
   // thin Q (m x kq, row-major): column c = H_0 ... H_c e_c, built in shared memory
@@ -417,7 +425,7 @@ static cudaError_t coop_launch(const void* fn, int grid, int block, void** args,
 template <typename T>
 static cudaError_t qr_launch(qtt_ctx* ctx, const double* Ain, Dim lda, double* Wd, long long ldw, Dim m, Dim n,
                              long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
-                             long long qm_max) {
+                             long long qm_max, int block) {
   int grid = (int)std::min<long long>(ctx->coop_blocks, std::max<long long>(nmax, 1));
   size_t smem = 0;
   if (Qout) smem = (size_t)qm_max * sizeof(T);
@@ -427,23 +435,28 @@ static cudaError_t qr_launch(qtt_ctx* ctx, const double* Ain, Dim lda, double* W
   int rrm = r_rowmajor ? 1 : 0;
   DevSync* sync = ctx->ws.d_sync;
   int* flag = ctx->ws.d_flags;
+  double* flops = g_flop_ctr;
   void* args[] = {(void*)&Ain, (void*)&lda, (void*)&W, (void*)&ldw, (void*)&m, (void*)&n, (void*)&tau,
                   (void*)&Rout, (void*)&rrm, (void*)&ldr, (void*)&Qout, (void*)&kq_out, (void*)&flag,
-                  (void*)&sync};
+                  (void*)&sync, (void*)&flops};
   // long columns (ldw bounds the rows): 1024 threads shorten each pass over a
   // column, which the reflector chain waits on
-  if (ldw >= 2048) return coop_launch((const void*)qr_kernel<T, 1024>, grid, 1024, args, smem, ctx->stream);
+  if (block == 0) block = ldw >= 2048 ? 1024 : NT;
+  if (block == 1024) return coop_launch((const void*)qr_kernel<T, 1024>, grid, 1024, args, smem, ctx->stream);
+  if (block != NT) return cudaErrorInvalidValue;
   return coop_launch((const void*)qr_kernel<T, NT>, grid, NT, args, smem, ctx->stream);
 }
 
 cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
-                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
-  return qr_launch<double>(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max);
+                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max,
+                   int block) {
+  return qr_launch<double>(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max, block);
 }
 
 cudaError_t qr_f32(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
-                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
-  return qr_launch<float>(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max);
+                   double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max,
+                   int block) {
+  return qr_launch<float>(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max, block);
 }
 
 cudaError_t jacobi_f64(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, double* J,
@@ -451,7 +464,7 @@ cudaError_t jacobi_f64(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lo
   long long pairs = (nvmax + 1) / 2;
   int grid = (int)std::min<long long>(ctx->coop_blocks, std::max<long long>(pairs, 1));
   DevSync* sync = ctx->ws.d_sync;
-  int max_sweeps = 100;
+  int max_sweeps = ctx->max_sweeps;
   // a pair counts as orthogonal when |v_i.v_j| <= 1e-13 |v_i||v_j| (above the
   // rounding floor of accumulated rotations) or <= 1e-15 max(|v_i|^2, |v_j|^2)
   double tol = 1e-13, tol_abs = 1e-15;

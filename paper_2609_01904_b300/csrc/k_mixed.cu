@@ -845,7 +845,7 @@ __global__ void scale_rows_kernel(const double* W, long long ldw, const double* 
 
 inline int eg(long long total) {
   long long g = (total + 255) / 256;
-  return (int)std::max(1LL, std::min(g, 148LL * 8));
+  return (int)std::max(1LL, std::min(g, device_sms() * 8LL));
 }
 
 }  // namespace
@@ -934,7 +934,7 @@ cudaError_t ns_factor(const double* G, double* H, long long ld, Dim n, long long
 
 cudaError_t omega_factor(const double* G, double* rs, double* M, long long ld, Dim n, long long nmax,
                          cudaStream_t st) {
-  omega_rowsum_kernel<<<(int)std::max(1LL, std::min(nmax, 148LL * 4)), 256, 0, st>>>(G, ld, n, rs);
+  omega_rowsum_kernel<<<(int)std::max(1LL, std::min(nmax, device_sms() * 4LL)), 256, 0, st>>>(G, ld, n, rs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   omega_kernel<<<eg(nmax * nmax), 256, 0, st>>>(G, rs, M, ld, n);
@@ -999,7 +999,7 @@ cudaError_t scale_rows(const double* W, long long ldw, const double* norms, Dim 
 }
 
 cudaError_t row_norms(const double* W, long long ldw, Dim n, Dim m, long long nmax, double* norms, cudaStream_t st) {
-  row_norms_kernel<<<(int)std::max(1LL, std::min(nmax, 148LL * 4)), 256, 0, st>>>(W, ldw, n, m, norms);
+  row_norms_kernel<<<(int)std::max(1LL, std::min(nmax, device_sms() * 4LL)), 256, 0, st>>>(W, ldw, n, m, norms);
   return cudaGetLastError();
 }
 

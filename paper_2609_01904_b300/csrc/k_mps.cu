@@ -10,10 +10,6 @@ namespace qtt {
 
 namespace {
 
-__device__ __forceinline__ int site_bit(long long ix, long long iz, int k, int n, int order) {
-  if (order == QTT_ORDER_SEQUENTIAL) return k < n ? (int)((ix >> k) & 1) : (int)((iz >> (k - n)) & 1);
-  return (k & 1) ? (int)((iz >> (k >> 1)) & 1) : (int)((ix >> (k >> 1)) & 1);
-}
 
 // T[(a,t)][(w',b')] = sum_{w,s} W[w][t][s][w'] X[(a,w)][(s,b')]
 __global__ void mpo_apply_lr_kernel(const double* __restrict__ X, double* __restrict__ T,
@@ -97,7 +93,7 @@ __global__ void mps_sum_kernel(SumArgs a) {
         if (k == 0) v *= a.coef[t];
       } else {  // rank-1 source: one-hot on the source's bits
         v = (s == a.src_bits[k]) ? 1.0 : 0.0;
-        if (k == 0) v *= a.src_amp_dev ? *a.src_amp_dev : a.src_amp;
+        if (k == 0) v *= (a.src_amp_dev ? *a.src_amp_dev : a.src_amp) * (a.amp_scale ? *a.amp_scale : 1.0);
       }
     }
     out[e] = v;
@@ -109,12 +105,15 @@ __global__ void sample_kernel(SampleArgs a) {
   double* v = sh;
   double* v2 = sh + a.rmax;
   for (long long p = blockIdx.x; p < a.count; p += gridDim.x) {
-    const long long ix = a.ix[p], iz = a.iz[p];
+    const long long N = 1LL << a.n;
+    long long lin = a.ix[p];
+    if (a.dims == 3) lin = lin * N + a.iy[p];
+    lin = lin * N + a.iz[p];
     if (threadIdx.x == 0) v[0] = 1.0;
     __syncthreads();
     int rl = 1;
     for (int k = 0; k < a.d; ++k) {
-      const int bit = site_bit(ix, iz, k, a.n, a.order);
+      const int bit = (int)((lin >> a.sp.pos[k]) & 1);
       const int rr = a.ranks[k + 1];
       const double* c = a.core[k];
       for (int j = threadIdx.x; j < rr; j += blockDim.x) {
@@ -193,17 +192,16 @@ __global__ void right_chain_kernel(ChainArgs a) {
   }
 }
 
-// dense[x*N+z] = S[L][R] with (L, R) the site bits of (x, z)
-__global__ void scatter_dense_kernel(const double* __restrict__ S, double* __restrict__ out, int n, int order,
-                                     int h) {
-  const long long N = 1LL << n, total = N * N;
-  const int d = 2 * n;
+// dense[i] = S[L][R] with (L, R) the site bits of dense index i: sites below h
+// give L, the others R
+__global__ void scatter_dense_kernel(const double* __restrict__ S, double* __restrict__ out, SitePos sp, int h) {
+  const int d = sp.d;
+  const long long total = 1LL << d;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long x = idx / N, z = idx % N;
     long long L = 0, R = 0;
     for (int k = 0; k < d; ++k) {
-      long long b = site_bit(x, z, k, n, order);
+      const long long b = (idx >> sp.pos[k]) & 1;
       if (k < h) L |= b << k;
       else R |= b << (k - h);
     }
@@ -211,26 +209,40 @@ __global__ void scatter_dense_kernel(const double* __restrict__ S, double* __res
   }
 }
 
-// site tensor t[Lin], Lin = sum_k s_k 2^(d-1-k) (site 0 slowest), from u[x*N+z]
-__global__ void site_permute_kernel(const double* __restrict__ u, double* __restrict__ t, int n, int order,
-                                    int square) {
-  const int d = 2 * n;
-  const long long N = 1LL << n, total = N * N;
+// site tensor t[Lin], Lin = sum_k s_k 2^(d-1-k) (site 0 slowest), from the dense u
+__global__ void site_permute_kernel(const double* __restrict__ u, double* __restrict__ t, SitePos sp, int square) {
+  const int d = sp.d;
+  const long long total = 1LL << d;
   for (long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x; lin < total;
        lin += (long long)gridDim.x * blockDim.x) {
-    long long x = 0, z = 0;
-    for (int k = 0; k < d; ++k) {
-      const long long s = (lin >> (d - 1 - k)) & 1;
-      if (order == QTT_ORDER_SEQUENTIAL) {
-        if (k < n) x |= s << k;
-        else z |= s << (k - n);
-      } else {
-        if (k & 1) z |= s << (k >> 1);
-        else x |= s << (k >> 1);
-      }
-    }
-    double v = u[x * N + z];
+    long long idx = 0;
+    for (int k = 0; k < d; ++k) idx |= ((lin >> (d - 1 - k)) & 1) << sp.pos[k];
+    const double v = u[idx];
     t[lin] = square ? v * v : v;
+  }
+}
+
+// Eq. 2 with the 7-point stencil (the 3D extension)
+__global__ void fdtd3_kernel(const double* __restrict__ c2, double lambda2, const double* __restrict__ up,
+                             const double* __restrict__ uc, double* __restrict__ un, int n, int bc, long long sx,
+                             long long sy, long long sz, double amp) {
+  const long long N = 1LL << n, M = N - 1, total = N * N * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long x = idx >> (2 * n), y = (idx >> n) & M, z = idx & M;
+    const double c = uc[idx];
+    double nb;
+    if (bc == QTT_BC_PERIODIC) {
+      nb = uc[((((x + 1) & M) * N + y) << n) + z] + uc[((((x - 1) & M) * N + y) << n) + z] +
+           uc[((x * N + ((y + 1) & M)) << n) + z] + uc[((x * N + ((y - 1) & M)) << n) + z] +
+           uc[((x * N + y) << n) + ((z + 1) & M)] + uc[((x * N + y) << n) + ((z - 1) & M)];
+    } else {
+      nb = (x + 1 < N ? uc[idx + N * N] : 0.0) + (x > 0 ? uc[idx - N * N] : 0.0) + (y + 1 < N ? uc[idx + N] : 0.0) +
+           (y > 0 ? uc[idx - N] : 0.0) + (z + 1 < N ? uc[idx + 1] : 0.0) + (z > 0 ? uc[idx - 1] : 0.0);
+    }
+    double v = 2.0 * c - up[idx] + lambda2 * c2[idx] * (nb - 6.0 * c);
+    if (x == sx && y == sy && z == sz) v += amp;
+    un[idx] = v;
   }
 }
 
@@ -290,10 +302,37 @@ __global__ void scale_rows_kernel(double* M, long long ldm, Dim ncols, const int
   }
 }
 
+__global__ void __launch_bounds__(256) state_scale_prepare_kernel(const double* a, const int* ra, const double* b,
+                                                                 const int* rb, double* scale) {
+  __shared__ double red[32];
+  double m = 0.0;
+  const long long na = 2LL * *ra, nb = 2LL * *rb;
+  for (long long i = threadIdx.x; i < na; i += blockDim.x) m = fmax(m, fabs(a[i]));
+  for (long long i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, fabs(b[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    m = fmax(m, red[0]);
+    int e = 0;
+    if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+    scale[0] = ldexp(1.0, -e);
+    scale[1] = ldexp(1.0, e);
+  }
+}
+
+__global__ void state_scale_apply_kernel(double* core, const int* r, const double* scale, int which) {
+  const long long n = 2LL * *r;
+  const double f = scale[which];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    core[i] *= f;
+}
+
 inline int grid_for(long long total, int nt) {
   long long g = (total + nt - 1) / nt;
   if (g < 1) g = 1;
-  if (g > 148 * 32) g = 148 * 32;
+  if (g > device_sms() * 32LL) g = device_sms() * 32LL;
   return (int)g;
 }
 
@@ -312,7 +351,7 @@ cudaError_t mps_sum(const SumArgs& a, long long max_core_elems, cudaStream_t st)
 }
 
 cudaError_t sample(const SampleArgs& a, cudaStream_t st) {
-  int g = (int)std::min<long long>(a.count, 148 * 8);
+  int g = (int)std::min<long long>(a.count, device_sms() * 8LL);
   if (g < 1) return cudaSuccess;
   sample_kernel<<<g, 128, 2 * a.rmax * sizeof(double), st>>>(a);
   return cudaGetLastError();
@@ -320,22 +359,39 @@ cudaError_t sample(const SampleArgs& a, cudaStream_t st) {
 
 cudaError_t chains(const ChainArgs& left, const ChainArgs& right, cudaStream_t st) {
   long long nL = 1LL << left.h, nR = 1LL << (right.d - right.h);
-  left_chain_kernel<<<(int)std::min<long long>(nL, 148 * 8), 128, 2 * left.rmax * sizeof(double), st>>>(left);
+  left_chain_kernel<<<(int)std::min<long long>(nL, device_sms() * 8LL), 128, 2 * left.rmax * sizeof(double), st>>>(left);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  right_chain_kernel<<<(int)std::min<long long>(nR, 148 * 8), 128, 2 * right.rmax * sizeof(double), st>>>(right);
+  right_chain_kernel<<<(int)std::min<long long>(nR, device_sms() * 8LL), 128, 2 * right.rmax * sizeof(double), st>>>(right);
   return cudaGetLastError();
 }
 
-cudaError_t scatter_dense(const double* S, double* out, int n, int order, int h, cudaStream_t st) {
-  long long total = 1LL << (2 * n);
-  scatter_dense_kernel<<<grid_for(total, 256), 256, 0, st>>>(S, out, n, order, h);
+cudaError_t state_scale_prepare(const double* a, const int* ra, const double* b, const int* rb, long long rmax,
+                                double* scale, cudaStream_t st) {
+  (void)rmax;
+  state_scale_prepare_kernel<<<1, 256, 0, st>>>(a, ra, b, rb, scale);
   return cudaGetLastError();
 }
 
-cudaError_t site_permute(const double* u, double* t, int n, int order, bool square, cudaStream_t st) {
-  long long total = 1LL << (2 * n);
-  site_permute_kernel<<<grid_for(total, 256), 256, 0, st>>>(u, t, n, order, square ? 1 : 0);
+cudaError_t state_scale_apply(double* core, const int* r, long long rmax, const double* scale, int which,
+                              cudaStream_t st) {
+  state_scale_apply_kernel<<<grid_for(2 * rmax, 256), 256, 0, st>>>(core, r, scale, which);
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_dense(const double* S, double* out, const SitePos& sp, int h, cudaStream_t st) {
+  scatter_dense_kernel<<<grid_for(1LL << sp.d, 256), 256, 0, st>>>(S, out, sp, h);
+  return cudaGetLastError();
+}
+
+cudaError_t site_permute(const double* u, double* t, const SitePos& sp, bool square, cudaStream_t st) {
+  site_permute_kernel<<<grid_for(1LL << sp.d, 256), 256, 0, st>>>(u, t, sp, square ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t fdtd3(const double* c2, double lambda2, const double* up, const double* uc, double* un, int n, int bc,
+                  long long sx, long long sy, long long sz, double amp, cudaStream_t st) {
+  fdtd3_kernel<<<grid_for(1LL << (3 * n), 256), 256, 0, st>>>(c2, lambda2, up, uc, un, n, bc, sx, sy, sz, amp);
   return cudaGetLastError();
 }
 

@@ -20,13 +20,23 @@ struct SumArgs {
   int src_bits[kMaxSites];
   double src_amp;
   const double* src_amp_dev;  // when set, the amplitude is read from here (graph replays)
+  const double* amp_scale;    // when set, the amplitude is multiplied by *amp_scale (state scaling)
+};
+
+// Encoding (Eq. 3, Eq. 12 order, Eq. 14-15): site k carries bit pos[k] of the
+// linear dense index ((x N + y) N + z in 3D, x N + z in 2D); see site_pos().
+struct SitePos {
+  int d;
+  int pos[kMaxSites];
 };
 
 struct SampleArgs {
-  int d, n, order, rmax;
+  int d, n, dims, rmax;
+  SitePos sp;
   const double* core[kMaxSites];
   const int* ranks;
   const long* ix;
+  const long* iy;  // 3D only
   const long* iz;
   long long count;
   double* out;
@@ -44,8 +54,11 @@ cudaError_t mpo_apply_lr(const double* X, double* T, const double* W, int w, int
 cudaError_t mps_sum(const SumArgs& a, long long max_core_elems, cudaStream_t st);
 cudaError_t sample(const SampleArgs& a, cudaStream_t st);
 cudaError_t chains(const ChainArgs& left, const ChainArgs& right, cudaStream_t st);
-cudaError_t scatter_dense(const double* S, double* out, int n, int order, int h, cudaStream_t st);
-cudaError_t site_permute(const double* u, double* t, int n, int order, bool square, cudaStream_t st);
+cudaError_t scatter_dense(const double* S, double* out, const SitePos& sp, int h, cudaStream_t st);
+cudaError_t site_permute(const double* u, double* t, const SitePos& sp, bool square, cudaStream_t st);
+// dense 7-point update of the 3D extension: arrays N^3, u[(x N + y) N + z]
+cudaError_t fdtd3(const double* c2, double lambda2, const double* up, const double* uc, double* un, int n, int bc,
+                  long long sx, long long sy, long long sz, double amp, cudaStream_t st);
 cudaError_t fdtd(const double* c2, double lambda2, const double* up, const double* uc, double* un, int n, int bc,
                  long long sx, long long sz, double amp, cudaStream_t st);
 cudaError_t copy2d(const double* src, double* dst, Dim R, Dim C, Dim ssi, Dim ssj, Dim dsi, Dim dsj,
@@ -54,6 +67,14 @@ cudaError_t init_zip(double* carry, int* ranks, int d, const int* copy_src, int*
                      cudaStream_t st);
 cudaError_t scale_rows(double* M, long long ldm, Dim ncols, const int* r_p, const double* sigma, long long total_max,
                        cudaStream_t st);
+// Power-of-two state scaling of the reduced-precision step: scale[0] = 2^s,
+// scale[1] = 2^-s with 2^s max(|a|, |b|) in [0.5, 1) over the first cores
+// a, b (1 x 2 x r, r = *ra / *rb) of two states (s = 0 for zero states);
+// then core <- core * scale[which] for a first core of rank *r (exact).
+cudaError_t state_scale_prepare(const double* a, const int* ra, const double* b, const int* rb, long long rmax,
+                                double* scale, cudaStream_t st);
+cudaError_t state_scale_apply(double* core, const int* r, long long rmax, const double* scale, int which,
+                              cudaStream_t st);
 
 // k_linalg.cu
 cudaError_t linalg_init(int device);

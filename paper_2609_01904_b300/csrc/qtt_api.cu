@@ -16,7 +16,10 @@
 #include "qtt_internal.cuh"
 
 namespace qtt {
-void build_laplacian(int n, int order, int bc, Mpo* mpo);
+void build_laplacian(int n, int order, int bc, int dims, Mpo* mpo);
+int site_pos(int k, int n, int order, int dims);
+void build_a_operator(const Mpo& L, const std::vector<std::vector<double>>& c2, const std::vector<int>& rc,
+                      double lambda2, Mpo* A);
 }
 
 using namespace qtt;
@@ -34,6 +37,19 @@ qtt_status fail(qtt_status s, const std::string& msg) {
 
 namespace qtt {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+thread_local double* g_flop_ctr = nullptr;
+
+int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  if (dev < 64) cache[dev] = n;
+  return n;
+}
 }  // namespace qtt
 
 namespace {
@@ -52,6 +68,7 @@ namespace {
   do {                                                                                         \
     prof_begin(ctx, cls);                                                                      \
     cudaError_t e_ = (call);                                                                   \
+    g_flop_ctr = nullptr;                                                                      \
     if (e_ != cudaSuccess)                                                                     \
       return fail(e_ == cudaErrorMemoryAllocation ? QTT_ENOMEM : QTT_ECUDA,                    \
                   std::string(#call) + ": " + cudaGetErrorString(e_));                         \
@@ -62,6 +79,7 @@ namespace {
 
 void prof_begin(qtt_ctx* ctx, int cls) {
   Prof& p = ctx->prof;
+  g_flop_ctr = p.d_flops ? p.d_flops + cls : nullptr;
   if (!p.timing) return;
   if (p.used >= (int)p.ev.size()) {
     cudaEvent_t a, b;
@@ -151,7 +169,7 @@ void ws_free(qtt_ctx* ctx) {
   Workspace& s = ctx->ws;
   double** bufs[] = {&s.d_carry, &s.d_x, &s.d_tv, &s.d_tq, &s.d_rv, &s.d_jv, &s.d_jp, &s.d_w1,
                      &s.d_tt, &s.d_qt, &s.d_jh, &s.d_rg, &s.d_rh, &s.d_rt, &s.d_rw, &s.d_tau,
-                     &s.d_sig, &s.d_norm, &s.d_disc};
+                     &s.d_sig, &s.d_norm, &s.d_disc, &s.d_scale};
   for (double** b : bufs)
     if (*b) {
       cudaFree(*b);
@@ -239,8 +257,8 @@ Sizes step_sizes(const qtt_ctx* ctx, const Caps& c, const std::vector<int>& w, c
 qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
   Workspace& s = ctx->ws;
   const int d = ctx->d;
-  const long long N2 = p2(2 * ctx->p.n);
-  // TT-SVD of a dense grid and to_dense use N^2-sized scratch
+  const long long N2 = p2(ctx->d);
+  // TT-SVD of a dense grid and to_dense use N^dims-sized scratch
   long long tv = std::max(z.tv, N2), carry = std::max(z.carry, N2), x = std::max(z.x, N2);
   s.carry = carry;
   s.xbuf = x;
@@ -270,10 +288,13 @@ qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
   CK(cudaMalloc(&s.d_sig, s.vec * sizeof(double)));
   CK(cudaMalloc(&s.d_norm, s.vec * sizeof(double)));
   CK(cudaMalloc(&s.d_disc, 3 * (d + 1) * sizeof(double)));
+  CK(cudaMalloc(&s.d_scale, 2 * sizeof(double)));
   CK(cudaMalloc(&s.d_ints, 4 * (d + 8) * sizeof(int)));
   CK(cudaMalloc(&s.d_flags, (s.vec + 64) * sizeof(int)));
   CK(cudaMalloc(&s.d_sync, sizeof(DevSync)));
   CK(cudaMemsetAsync(s.d_sync, 0, sizeof(DevSync), ctx->stream));
+  CK(cudaMemcpyAsync(&s.d_sync->limit_ns, &ctx->wait_limit_ns, sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                     ctx->stream));
   CK(cudaMemsetAsync(s.d_disc, 0, 3 * (d + 1) * sizeof(double), ctx->stream));
   CK(cudaMalloc(&s.d_spec, (d + 1) * z.nvmax * sizeof(double)));
   CK(cudaMalloc(&s.d_spec_len, (d + 1) * sizeof(int)));
@@ -303,9 +324,22 @@ qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
   return QTT_OK;
 }
 
+// Capacities of the fused step (Eq. 7 applied as one MPO A of bonds w):
+// theta = phi - psi^{k-1} (+ source) needs phi + psi + 1 at every bond.
+Caps fused_caps(const qtt_ctx* ctx, const std::vector<int>& w) {
+  Caps c = step_caps(ctx, w, std::vector<int>(ctx->d + 1, 1));
+  for (int k = 1; k < ctx->d; ++k) c.theta[k] = std::max(c.theta[k], c.phi[k] + c.psi[k] + 1);
+  return c;
+}
+
+qtt_status ensure_ws_caps(qtt_ctx* ctx, const std::vector<int>& w, const std::vector<int>& rc, const Caps& c);
+
 // Workspace for a step with MPO bonds w and c^2 ranks rc (grown if needed).
 qtt_status ensure_ws(qtt_ctx* ctx, const std::vector<int>& w, const std::vector<int>& rc) {
-  Caps c = step_caps(ctx, w, rc);
+  return ensure_ws_caps(ctx, w, rc, step_caps(ctx, w, rc));
+}
+
+qtt_status ensure_ws_caps(qtt_ctx* ctx, const std::vector<int>& w, const std::vector<int>& rc, const Caps& c) {
   Sizes z = step_sizes(ctx, c, w, rc);
   if (ctx->ws_ready) {
     const Workspace& s = ctx->ws;
@@ -332,7 +366,11 @@ qtt_status device_status(qtt_ctx* ctx) {
   CK(cudaMemcpyAsync(&st, &ctx->ws.d_sync->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (st != 0) {
+    // a kernel that gave up leaves barrier counters and flags mid-way: reset
+    // the whole word (keeping the context's wait limit) before the next launch
     CK(cudaMemsetAsync(ctx->ws.d_sync, 0, sizeof(DevSync), ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->ws.d_sync->limit_ns, &ctx->wait_limit_ns, sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const char* what = st == QTT_ENOCONV ? "Jacobi SVD reached its sweep limit"
                        : st == QTT_ETIMEOUT ? "a grid barrier wait timed out"
@@ -342,6 +380,25 @@ qtt_status device_status(qtt_ctx* ctx) {
   }
   return QTT_OK;
 }
+
+// Site positions of the context (Eq. 3, Eq. 12, Eq. 14-15; 3D extension).
+SitePos site_positions(const qtt_ctx* ctx) {
+  SitePos sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.d = ctx->d;
+  for (int k = 0; k < ctx->d; ++k) sp.pos[k] = ctx->site_pos[k];
+  return sp;
+}
+
+// A grid point given as dims coordinates, each in [0, N).
+qtt_status check_point(const qtt_ctx* ctx, const long* p) {
+  const long N = 1L << ctx->p.n;
+  for (int a = 0; a < ctx->dims; ++a)
+    if (p[a] < 0 || p[a] >= N) return fail(QTT_EINVAL, "point outside the grid");
+  return QTT_OK;
+}
+
+qtt_status inject_impl(qtt_ctx* ctx, qtt_mps* psi, const long* src, double amp);
 
 // ------------------------------------------------------------- SVD helper
 // Truncated SVD of nv vectors (rows of the vector-major array Tv, ld ell,
@@ -358,15 +415,60 @@ GemmArgs gemm0();
 
 namespace {
 
+// columns per CTA of a tensor-core contraction: the widest tile that still
+// gives every SM a CTA, else the narrowest
+int tc_tile_n(const qtt_ctx* ctx, long long Mmax, long long Nmax, long long nb) {
+  const long long tiles_m = (Mmax + 127) / 128 * nb;
+  for (int bn : {256, 128}) {
+    if (Nmax <= bn / 2) continue;
+    if (tiles_m * ((Nmax + bn - 1) / bn) >= ctx->num_sms) return bn;
+  }
+  return Nmax <= 64 ? 64 : (Nmax <= 128 && tiles_m * 2 < ctx->num_sms ? 64 : 128);
+}
+
+int tune_choice(const qtt_ctx* ctx, int op, int kind, long long a, long long b, long long c) {
+  if (ctx->tune.empty()) return 0;
+  auto it = ctx->tune.find(TuneKey{op, kind, a, b, c});
+  return it == ctx->tune.end() ? 0 : it->second;
+}
+
+// A contraction GEMM of the given kind (0 FP64, 1 FP32 SIMT, 2.. tensor
+// cores) with the autotuned tile of its bucket; recorded when a dry-run step
+// is being recorded.
+cudaError_t gemm_k(qtt_ctx* ctx, int kind, const GemmArgs& g, long long Mmax, long long Nmax, long long b1,
+                   long long b2) {
+  const long long nb = b1 * b2;
+  auto run = [ctx, kind, g, Mmax, Nmax, b1, b2, nb](int ch) -> cudaError_t {
+    if (kind == 0) return gemm_f64(g, Mmax, Nmax, b1, b2, ctx->stream, ch);
+    if (kind == 1) return gemm_f32(g, Mmax, Nmax, b1, b2, ctx->stream, ch);
+    return gemm_tc(g, Mmax, Nmax, b1, b2, kind - 2, ch ? ch : tc_tile_n(ctx, Mmax, Nmax, nb), ctx->ws.d_sync,
+                   ctx->stream);
+  };
+  if (ctx->tune_rec) ctx->tune_rec->push_back(TuneRec{0, kind, Mmax, Nmax, nb, run});
+  return run(tune_choice(ctx, 0, kind, Mmax, Nmax, nb));
+}
+
 // contractions and QR in the step's precision; setup work is always FP64
 cudaError_t gemm_any(qtt_ctx* ctx, const GemmArgs& g, long long Mmax, long long Nmax, long long b1, long long b2) {
-  return ctx->use_mp ? gemm_f32(g, Mmax, Nmax, b1, b2, ctx->stream) : gemm_f64(g, Mmax, Nmax, b1, b2, ctx->stream);
+  return gemm_k(ctx, !ctx->use_mp ? 0 : (ctx->ckind < 0 ? 1 : ctx->ckind + 2), g, Mmax, Nmax, b1, b2);
+}
+
+// an FP64 GEMM of the refinement or the Gram matrix (autotuned like the rest)
+cudaError_t gemm_d(qtt_ctx* ctx, const GemmArgs& g, long long Mmax, long long Nmax, long long b1, long long b2,
+                   cudaStream_t) {
+  return gemm_k(ctx, 0, g, Mmax, Nmax, b1, b2);
 }
 
 cudaError_t qr_any(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n, long long nmax,
                    double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr, long long qm_max) {
-  return ctx->use_mp ? qr_f32(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max)
-                     : qr_f64(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max);
+  const int kind = ctx->use_mp ? 1 : 0;
+  auto run = [=](int ch) -> cudaError_t {
+    return kind ? qr_f32(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max, ch)
+                : qr_f64(ctx, Ain, lda, W, ldw, m, n, nmax, Rout, r_rowmajor, Qout, kq_out, ldr, qm_max, ch);
+  };
+  const long long withq = Qout ? 1 : 0;
+  if (ctx->tune_rec) ctx->tune_rec->push_back(TuneRec{1, kind, ldw, nmax, withq, run});
+  return run(tune_choice(ctx, 1, kind, ldw, nmax, withq));
 }
 
 // C (ld ldc) = A B with A (M x K, ld lda) and B (K x N, ld ldb), FP64
@@ -411,25 +513,25 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
   if (mmax > ld || nvmax > ld) return fail(QTT_EINVAL, "internal: mixed SVD wider than the workspace");
   KL(KC_JACOBI, jacobi32_cluster(ctx, V, ldv, nv, m, nvmax, mmax, J, ldj));
   auto ns = [&]() -> qtt_status {  // J <- (3I - J J^T)/2 J  (rows of J are the columns of the rotation)
-    KL(KC_REFINE, gemm_f64(gram(J, ldj, s.d_rg, ld, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_d(ctx, gram(J, ldj, s.d_rg, ld, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
     KL(KC_REFINE, ns_factor(s.d_rg, s.d_rh, ld, nv, nvmax, ctx->stream));
-    KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_d(ctx, mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
     KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
                          ctx->stream));
     return QTT_OK;
   };
   for (int it = 0; it < 2; ++it) {
     CKS(ns());
-    KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
-    KL(KC_REFINE, gemm_f64(gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_d(ctx, mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_d(ctx, gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
     KL2(KC_REFINE, omega_factor(s.d_rg, norms, s.d_rh, ld, nv, nvmax, ctx->stream));  // two kernels; norms: scratch
-    KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_d(ctx, mm(s.d_rh, ld, J, ldj, s.d_rt, ld, nv, nv, nv), nvmax, nvmax, 1, 1, ctx->stream));
     KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
                          ctx->stream));
   }
   CKS(ns());
   CKS(ns());
-  KL(KC_REFINE, gemm_f64(mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
+  KL(KC_REFINE, gemm_d(ctx, mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
   KL(KC_REFINE, row_norms(s.d_rw, ld, nv, m, nvmax, norms, ctx->stream));
   return QTT_OK;
 }
@@ -439,9 +541,9 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
 qtt_status ns_rows(qtt_ctx* ctx, double* J, long long ldj, Dim rows, Dim cols, long long rowsmax, long long colsmax) {
   Workspace& s = ctx->ws;
   const long long ld = ctx->ws_nvmax;
-  KL(KC_REFINE, gemm_f64(gram(J, ldj, s.d_rg, ld, rows, cols), rowsmax, rowsmax, 1, 1, ctx->stream));
+  KL(KC_REFINE, gemm_d(ctx, gram(J, ldj, s.d_rg, ld, rows, cols), rowsmax, rowsmax, 1, 1, ctx->stream));
   KL(KC_REFINE, ns_factor(s.d_rg, s.d_rh, ld, rows, rowsmax, ctx->stream));
-  KL(KC_REFINE, gemm_f64(mm(s.d_rh, ld, J, ldj, s.d_rt, ld, rows, rows, cols), rowsmax, colsmax, 1, 1, ctx->stream));
+  KL(KC_REFINE, gemm_d(ctx, mm(s.d_rh, ld, J, ldj, s.d_rt, ld, rows, rows, cols), rowsmax, colsmax, 1, 1, ctx->stream));
   KL(KC_REFINE, copy2d(s.d_rt, J, rows, cols, dconst(ld), dconst(1), dconst(ldj), dconst(1), rowsmax * colsmax, 1.0,
                        ctx->stream));
   return QTT_OK;
@@ -491,7 +593,7 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     g.sbj = ell;
     g.sci = dconst(ldv);
     g.scj = dconst(1);
-    KL(KC_PIVOT, gemm_f64(g, nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_PIVOT, gemm_d(ctx, g, nvmax, nvmax, 1, 1, ctx->stream));
     KL(KC_PIVOT, pchol_cluster(ctx, s.d_tt, ldv, nv, ell, nvmax, s.d_rv, ldv, kr));
     CKS(jacobi_any(ctx, s.d_rv, ldv, dptr(kr), nv, nvmax, nvmax, s.d_jv, ldv, s.d_norm));
     // jacobi_any leaves W = J R in the refinement buffer
@@ -527,7 +629,7 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     g.sbj = dconst(ldv);
     g.sci = dconst(ldv);
     g.scj = dconst(1);
-    KL(KC_REFINE, gemm_f64(g, nvmax, nvmax, 1, 1, ctx->stream));
+    KL(KC_REFINE, gemm_d(ctx, g, nvmax, nvmax, 1, 1, ctx->stream));
     CKS(ns_rows(ctx, s.d_jh, ldv, dptr(k1), nv, nvmax, nvmax));
     KL(KC_POST, svd_post(ctx, s.d_norm, dptr(k1), dptr(kq), nv, s.d_jh, ldv, eps, chi, rank_cap, rank_out, sig,
                          disc_out, Jp, Jt, nsv_out));
@@ -727,7 +829,7 @@ qtt_status zipup_C(qtt_ctx* ctx, const Mps* c2, const std::vector<int>& rc, cons
 
 // -------------------------------------------------------------------- sum
 qtt_status form_sum(qtt_ctx* ctx, const std::vector<std::pair<double, const Mps*>>& terms, const long* src,
-                    double amp, Mps* out) {
+                    double amp, Mps* out, const double* amp_scale = nullptr) {
   const int d = ctx->d;
   SumArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -743,20 +845,11 @@ qtt_status form_sum(qtt_ctx* ctx, const std::vector<std::pair<double, const Mps*
   a.has_src = src ? 1 : 0;
   a.src_amp = amp;
   a.src_amp_dev = ctx->capturing ? ctx->d_amp : nullptr;
-  if (src) {
-    const int n = ctx->p.n;
-    for (int k = 0; k < d; ++k) {
-      long long v;
-      int b;
-      if (ctx->p.order == QTT_ORDER_SEQUENTIAL) {
-        v = k < n ? src[0] : src[1];
-        b = k < n ? k : k - n;
-      } else {
-        v = (k & 1) ? src[1] : src[0];
-        b = k >> 1;
-      }
-      a.src_bits[k] = (int)((v >> b) & 1);
-    }
+  a.amp_scale = amp_scale;
+  if (src) {  // the point's linear dense index, then the bit each site carries
+    long long lin = 0;
+    for (int a_ = 0; a_ < ctx->dims; ++a_) lin = (lin << ctx->p.n) | src[a_];
+    for (int k = 0; k < d; ++k) a.src_bits[k] = (int)((lin >> ctx->site_pos[k]) & 1);
   }
   long long mx = 1;
   for (int k = 0; k < d; ++k) mx = std::max(mx, (long long)out->cap[k] * 2 * out->cap[k + 1]);
@@ -990,7 +1083,8 @@ qtt_status tt_svd(qtt_ctx* ctx, const double* grid_dev, bool square, double eps,
   const int d = ctx->d, n = ctx->p.n;
   double* cur = s.d_carry;
   double* nxt = s.d_x;
-  KL(KC_OTHER, site_permute(grid_dev, cur, n, ctx->p.order, square, ctx->stream));
+  (void)n;
+  KL(KC_OTHER, site_permute(grid_dev, cur, site_positions(ctx), square, ctx->stream));
   KL(KC_OTHER, init_zip(nullptr, out->ranks, d, nullptr, nullptr, 0, ctx->stream));
   for (int k = 0; k < d - 1; ++k) {
     const long long ell = p2(d - k - 1);
@@ -1064,11 +1158,14 @@ const char* qtt_last_error(void) { return g_err.c_str(); }
 qtt_status qtt_ctx_create(const qtt_params* p, void* stream, qtt_ctx** out) {
   if (!p || !out) return fail(QTT_EINVAL, "null argument");
   *out = nullptr;
+  if (p->dims != 0 && p->dims != 2 && p->dims != 3) return fail(QTT_EINVAL, "dims must be 2 or 3 (0 = 2)");
   if (p->n < 1 || p->n > 14) return fail(QTT_EINVAL, "n must be in 1..14");
+  if (p->dims == 3 && p->n > 9) return fail(QTT_EINVAL, "n must be in 1..9 in 3D (3n <= 27 sites)");
   if (p->order != QTT_ORDER_SEQUENTIAL && p->order != QTT_ORDER_INTERLEAVED) return fail(QTT_EINVAL, "bad order");
   if (p->bc != QTT_BC_PERIODIC && p->bc != QTT_BC_ZERO) return fail(QTT_EINVAL, "bad boundary condition");
-  if (p->prec != QTT_FP64 && p->prec != QTT_FP32)
-    return fail(QTT_EINVAL, "prec must be QTT_FP64 or QTT_FP32 (TF32/BF16 contractions are not built)");
+  if (p->prec != QTT_FP64 && p->prec != QTT_FP32 && p->prec != QTT_TF32 && p->prec != QTT_TF32X3 &&
+      p->prec != QTT_BF16)
+    return fail(QTT_EINVAL, "prec must be one of QTT_FP64, QTT_FP32, QTT_TF32, QTT_TF32X3, QTT_BF16");
   if (p->chi_max < 1 || p->chi_max > 1024) return fail(QTT_EINVAL, "chi_max must be in 1..1024");
   if (!(p->eps >= 0.0 && p->eps < 1.0)) return fail(QTT_EINVAL, "eps must be in [0, 1)");
   if (p->chi_zip < 0 || p->chi_zip > 1024 || p->chi_c < 0 || p->chi_c > 1024)
@@ -1081,12 +1178,17 @@ qtt_status qtt_ctx_create(const qtt_params* p, void* stream, qtt_ctx** out) {
   if (!(c->p.eps_zip > 0.0)) c->p.eps_zip = c->p.eps;
   if (c->p.chi_c == 0) c->p.chi_c = c->p.chi_max;
   if (!(c->p.eps_c > 0.0)) c->p.eps_c = 1e-8;
-  c->d = 2 * p->n;
+  c->dims = p->dims == 3 ? 3 : 2;
+  c->p.dims = c->dims;
+  c->d = c->dims * p->n;
+  for (int k = 0; k < c->d; ++k) c->site_pos[k] = site_pos(k, p->n, p->order, c->dims);
   c->stream = (cudaStream_t)stream;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = linalg_init(c->device);
   if (e == cudaSuccess) e = mixed_init();
+  if (e == cudaSuccess) e = tc_init();
+  c->ckind = p->prec == QTT_TF32 ? 0 : p->prec == QTT_TF32X3 ? 1 : p->prec == QTT_BF16 ? 2 : -1;
   if (e != cudaSuccess) {
     delete c;
     return fail(QTT_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
@@ -1105,9 +1207,29 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
     cudaEventDestroy(e.second);
   }
   if (ctx->prof.d_log) cudaFree(ctx->prof.d_log);
+  if (ctx->prof.d_flops) cudaFree(ctx->prof.d_flops);
   if (ctx->d_amp) cudaFree(ctx->d_amp);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   delete ctx;
+}
+
+qtt_status qtt_set_limits(qtt_ctx* ctx, double wait_limit_s, int max_sweeps) {
+  if (!ctx) return fail(QTT_EINVAL, "null context");
+  if (!(wait_limit_s <= 3600.0)) return fail(QTT_EINVAL, "wait_limit_s must be <= 3600 (<= 0: the default)");
+  if (max_sweeps > 100000) return fail(QTT_EINVAL, "max_sweeps must be <= 100000 (<= 0: the default)");
+  ctx->wait_limit_ns = wait_limit_s > 0.0 ? std::max(1ULL, (unsigned long long)(wait_limit_s * 1e9)) : 0ULL;
+  ctx->max_sweeps = max_sweeps > 0 ? max_sweeps : 100;
+  for (auto& g : ctx->gexec)  // the sweep limit is a launch argument of the captured kernels
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  if (ctx->ws_ready) {
+    CK(cudaMemcpyAsync(&ctx->ws.d_sync->limit_ns, &ctx->wait_limit_ns, sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return QTT_OK;
 }
 
 qtt_status qtt_ctx_sync(qtt_ctx* ctx) {
@@ -1241,7 +1363,7 @@ static qtt_status from_dense_impl(qtt_ctx* ctx, const double* grid, int on_devic
                                   qtt_mps** out) {
   if (!ctx || !grid || !out) return fail(QTT_EINVAL, "null argument");
   CKS(ensure_ws_basic(ctx));
-  const long long N2 = p2(2 * ctx->p.n);
+  const long long N2 = p2(ctx->d);
   const double* g = grid;
   double* tmp = nullptr;
   if (!on_device) {
@@ -1290,7 +1412,7 @@ qtt_status qtt_velocity_mps(qtt_ctx* ctx, const double* c_grid, int on_device, q
 qtt_status qtt_laplacian_mpo(qtt_ctx* ctx, qtt_mpo** out) {
   if (!ctx || !out) return fail(QTT_EINVAL, "null argument");
   qtt_mpo* m = new qtt_mpo();
-  build_laplacian(ctx->p.n, ctx->p.order, ctx->p.bc, m);
+  build_laplacian(ctx->p.n, ctx->p.order, ctx->p.bc, ctx->dims, m);
   cudaError_t e = cudaMalloc(&m->data, m->host.size() * sizeof(double));
   if (e == cudaSuccess)
     e = cudaMemcpy(m->data, m->host.data(), m->host.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -1317,22 +1439,55 @@ void qtt_mpo_destroy(qtt_mpo* L) {
 
 qtt_status qtt_inject_source(qtt_ctx* ctx, qtt_mps* psi, long ix, long iz, double amp) {
   if (!ctx || !psi) return fail(QTT_EINVAL, "null argument");
-  const long N = 1L << ctx->p.n;
-  if (ix < 0 || ix >= N || iz < 0 || iz >= N) return fail(QTT_EINVAL, "source outside the grid");
-  CKS(ensure_ws_basic(ctx));
-  Workspace& s = ctx->ws;
-  // theta needs room for psi + 1
-  for (int k = 1; k < ctx->d; ++k)
-    if (s.theta->cap[k] < psi->cap[k] + 1) return fail(QTT_EINVAL, "internal: sum workspace too small");
-  long src[2] = {ix, iz};
-  CKS(form_sum(ctx, {{1.0, psi}}, src, amp, s.theta));
-  CKS(tt_round(ctx, s.theta, psi));
-  return QTT_OK;
+  if (ctx->dims != 2) return fail(QTT_EINVAL, "3D context: use qtt_inject_source_3d");
+  const long src[3] = {ix, iz, 0};
+  return inject_impl(ctx, psi, src, amp);
+}
+
+qtt_status qtt_inject_source_3d(qtt_ctx* ctx, qtt_mps* psi, long ix, long iy, long iz, double amp) {
+  if (!ctx || !psi) return fail(QTT_EINVAL, "null argument");
+  if (ctx->dims != 3) return fail(QTT_EINVAL, "2D context: use qtt_inject_source");
+  const long src[3] = {ix, iy, iz};
+  return inject_impl(ctx, psi, src, amp);
 }
 
 }  // extern "C"
 
 namespace {
+qtt_status inject_impl(qtt_ctx* ctx, qtt_mps* psi, const long* src_in, double amp) {
+  CKS(check_point(ctx, src_in));
+  CKS(ensure_ws_basic(ctx));
+  Workspace& s = ctx->ws;
+  // theta needs room for psi + 1
+  for (int k = 1; k < ctx->d; ++k)
+    if (s.theta->cap[k] < psi->cap[k] + 1) return fail(QTT_EINVAL, "internal: sum workspace too small");
+  CKS(form_sum(ctx, {{1.0, psi}}, src_in, amp, s.theta));
+  CKS(tt_round(ctx, s.theta, psi));
+  return QTT_OK;
+}
+}  // namespace
+
+namespace {
+
+// Reduced-precision steps only: the step is linear and its truncation rule
+// relative, so both states (their first cores carry the norm) and the source
+// sample are scaled by an exact power of two that brings the field to order
+// one before the FP32 / tensor-core arithmetic (whose exponent range ends at
+// ~1e-38: a field of 1e-10 with components kept down to 1e-10 of it would
+// underflow in the squared norms), and the result is scaled back.
+// phase 0: choose 2^s and scale u^{k-1}, u^k; phase 1: unscale the result
+// (in prev) and restore u^k.  Exact in FP64.
+qtt_status scale_states(qtt_ctx* ctx, Mps* prev, Mps* cur, int phase) {
+  if (!ctx->use_mp) return QTT_OK;
+  Workspace& s = ctx->ws;
+  const long long r1 = std::max(prev->cap[1], cur->cap[1]);
+  if (phase == 0)
+    KL(KC_OTHER, state_scale_prepare(cur->core(0), cur->ranks + 1, prev->core(0), prev->ranks + 1, r1, s.d_scale,
+                                     ctx->stream));
+  KL(KC_OTHER, state_scale_apply(prev->core(0), prev->ranks + 1, r1, s.d_scale, phase, ctx->stream));
+  KL(KC_OTHER, state_scale_apply(cur->core(0), cur->ranks + 1, r1, s.d_scale, phase, ctx->stream));
+  return QTT_OK;
+}
 
 // The launches of one step (Eq. 17): zip-up of L, zip-up of diag(c^2), the
 // sum with the source, the round into prev.  No host synchronisation.
@@ -1341,13 +1496,16 @@ qtt_status step_body(qtt_ctx* ctx, const Mpo* L, const Mps* c2, const std::vecto
   Workspace& s = ctx->ws;
   struct MpScope {  // the reduced-precision form applies inside the step only
     qtt_ctx* c;
-    explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec == QTT_FP32); }
+    explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec != QTT_FP64); }
     ~MpScope() { c->use_mp = false; }
   } mp_scope(ctx);
+  CKS(scale_states(ctx, prev, cur, 0));
   CKS(zipup_L(ctx, L, cur, s.phi, c));
   CKS(zipup_C(ctx, c2, rc, s.phi, s.eta, c));
-  CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta));
+  CKS(form_sum(ctx, {{2.0, cur}, {-1.0, prev}, {lambda2, s.eta}}, src, amp, s.theta,
+               ctx->use_mp ? s.d_scale : nullptr));
   CKS(tt_round(ctx, s.theta, prev));
+  CKS(scale_states(ctx, prev, cur, 1));
   return QTT_OK;
 }
 
@@ -1358,9 +1516,7 @@ qtt_status step_checks(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double
     return fail(QTT_EINVAL, "handle from another grid size");
   if (prev == cur) return fail(QTT_EINVAL, "psi_prev and psi_cur must differ");
   if (!(lambda2 >= 0.0) || !std::isfinite(lambda2)) return fail(QTT_EINVAL, "lambda2 must be finite, >= 0");
-  const long N = 1L << ctx->p.n;
-  if (src && (src[0] < 0 || src[0] >= N || src[1] < 0 || src[1] >= N))
-    return fail(QTT_EINVAL, "source outside the grid");
+  if (src) CKS(check_point(ctx, src));
   return QTT_OK;
 }
 
@@ -1386,16 +1542,19 @@ qtt_status qtt_step_graph(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, dou
   CKS(step_checks(ctx, L, c2, lambda2, prev, cur, src));
   if (ctx->p.use_learned_rank) return fail(QTT_EINVAL, "the learned rounding synchronises with the host: use qtt_step");
   if (ctx->prof.timing) return fail(QTT_EINVAL, "per-kernel timing is on: use qtt_step");
+  if (ctx->prof.d_log || ctx->prof.d_flops)
+    return fail(QTT_EINVAL, "work logging is on (qtt_profile_start log_svd): use qtt_step");
   std::vector<int> rc = c2->cap;
   if (c2->host_ranks.size() == (size_t)ctx->d + 1) rc = c2->host_ranks;
   CKS(ensure_ws(ctx, L->w, rc));
   Caps c = step_caps(ctx, L->w, rc);
   if (!ctx->d_amp) CK(cudaMalloc(&ctx->d_amp, sizeof(double)));
-  const long sk[3] = {src ? 1L : 0L, src ? src[0] : 0L, src ? src[1] : 0L};
+  const long sk[4] = {src ? 1L : 0L, src ? src[0] : 0L, src ? src[1] : 0L,
+                      (src && ctx->dims == 3) ? src[2] : 0L};
   auto same = [&](int g) {
     return ctx->gexec[g] && ctx->gkey[g][0] == L && ctx->gkey[g][1] == c2 && ctx->gkey[g][2] == prev->data &&
            ctx->gkey[g][3] == cur->data && ctx->gkey_lam == lambda2 && ctx->gkey_src[0] == sk[0] &&
-           ctx->gkey_src[1] == sk[1] && ctx->gkey_src[2] == sk[2];
+           ctx->gkey_src[1] == sk[1] && ctx->gkey_src[2] == sk[2] && ctx->gkey_src[3] == sk[3];
   };
   int g = same(0) ? 0 : (same(1) ? 1 : -1);
   if (g < 0) {  // capture the step for both roles of the pair of state buffers
@@ -1436,13 +1595,174 @@ qtt_status qtt_step_graph(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, dou
       swap_roles(prev, cur);  // the second graph serves the exchanged roles
     }
     ctx->gkey_lam = lambda2;
-    for (int k = 0; k < 3; ++k) ctx->gkey_src[k] = sk[k];
+    for (int k = 0; k < 4; ++k) ctx->gkey_src[k] = sk[k];
     g = 0;
   }
   CK(cudaMemcpyAsync(ctx->d_amp, &amp, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaGraphLaunch(ctx->gexec[g], ctx->stream));
   for (int k = 0; k < KC_N; ++k) ctx->prof.launches[k] += ctx->glaunches[k];
   swap_roles(prev, cur);
+  return QTT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Cache file of qtt_autotune: a small JSON document, one entry per line.
+std::string tune_header(const qtt_ctx* ctx, const std::vector<int>& rc) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, ctx->device);
+  const int rcmax = rc.empty() ? 1 : *std::max_element(rc.begin(), rc.end());
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "device=%s sms=%d prec=%d n=%d chi=%d chi_zip=%d order=%d bc=%d rc_max=%d",
+                prop.name, ctx->num_sms, ctx->p.prec, ctx->p.n, ctx->p.chi_max, ctx->p.chi_zip, ctx->p.order,
+                ctx->p.bc, rcmax);
+  return buf;
+}
+
+bool tune_load(const char* path, const std::string& header, std::map<TuneKey, int>* out) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  if (text.find("\"header\": \"" + header + "\"") == std::string::npos) return false;
+  std::map<TuneKey, int> m;
+  size_t pos = 0;
+  while ((pos = text.find("{\"op\": ", pos)) != std::string::npos) {
+    int op = 0, kind = 0, choice = 0;
+    long long a = 0, b = 0, c = 0;
+    if (std::sscanf(text.c_str() + pos, "{\"op\": %d, \"kind\": %d, \"a\": %lld, \"b\": %lld, \"c\": %lld, \"choice\": %d",
+                    &op, &kind, &a, &b, &c, &choice) == 6)
+      m[TuneKey{op, kind, a, b, c}] = choice;
+    pos += 8;
+  }
+  if (m.empty()) return false;
+  *out = m;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+qtt_status qtt_autotune(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, const qtt_mps* prev,
+                        const qtt_mps* cur, const char* cache_path, int reps, int* entries_out) {
+  CKS(step_checks(ctx, L, c2, lambda2, const_cast<qtt_mps*>(prev), const_cast<qtt_mps*>(cur), nullptr));
+  if (reps < 1 || reps > 1000) return fail(QTT_EINVAL, "reps must be in 1..1000");
+  if (ctx->prof.timing || ctx->prof.d_log) return fail(QTT_EINVAL, "profiling is on: stop it before autotuning");
+  if (ctx->p.use_learned_rank) return fail(QTT_EINVAL, "autotune a context without the learned rounding");
+  std::vector<int> rc = c2->cap;
+  if (c2->host_ranks.size() == (size_t)ctx->d + 1) rc = c2->host_ranks;
+  CKS(ensure_ws(ctx, L->w, rc));
+  const Caps caps = step_caps(ctx, L->w, rc);
+  const std::string header = tune_header(ctx, rc);
+  drop_graphs(ctx);  // the choices are launch parameters of captured graphs
+  if (cache_path && tune_load(cache_path, header, &ctx->tune)) {
+    if (entries_out) *entries_out = (int)ctx->tune.size();
+    return QTT_OK;
+  }
+  ctx->tune.clear();
+  // dry-run step on copies of the states, recording every tunable launch
+  Mps tp, tc;
+  CKS(mps_alloc(ctx, prev->cap, &tp));
+  qtt_status st = mps_alloc(ctx, cur->cap, &tc);
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    mps_free(&tp);
+    mps_free(&tc);
+  };
+  if (st == QTT_OK) {
+    const cudaError_t e1 = cudaMemcpyAsync(tp.data, prev->data, prev->total * sizeof(double), cudaMemcpyDeviceToDevice,
+                                           ctx->stream);
+    const cudaError_t e2 = cudaMemcpyAsync(tc.data, cur->data, cur->total * sizeof(double), cudaMemcpyDeviceToDevice,
+                                           ctx->stream);
+    const cudaError_t e3 = cudaMemcpyAsync(tp.ranks, prev->ranks, (ctx->d + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
+                                           ctx->stream);
+    const cudaError_t e4 = cudaMemcpyAsync(tc.ranks, cur->ranks, (ctx->d + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
+                                           ctx->stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess)
+      st = fail(QTT_ECUDA, "autotune: state copy");
+  }
+  std::vector<TuneRec> recs;
+  if (st == QTT_OK) {
+    ctx->tune_rec = &recs;
+    st = step_body(ctx, L, c2, rc, caps, lambda2, &tp, &tc, nullptr, 0.0);
+    ctx->tune_rec = nullptr;
+  }
+  if (st == QTT_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(QTT_ECUDA, "autotune: dry run");
+  if (st == QTT_OK) st = device_status(ctx);
+  if (st != QTT_OK) {
+    cleanup();
+    return st;
+  }
+  // time every candidate on all launches of its bucket (the step's own
+  // arguments and device-side sizes), keep the fastest
+  std::map<TuneKey, std::vector<const TuneRec*>> buckets;
+  for (const TuneRec& r : recs) buckets[TuneKey{r.op, r.kind, r.a, r.b, r.c}].push_back(&r);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::string body;
+  for (const auto& kv : buckets) {
+    const int op = std::get<0>(kv.first), kind = std::get<1>(kv.first);
+    std::vector<int> cand;
+    if (op == 1) cand = {256, 1024};
+    else if (kind <= 1) cand = {16, 32};
+    else cand = {64, 128, 256};
+    int best = 0;
+    double best_us = 1e300;
+    std::string times;
+    for (int ch : cand) {
+      bool ok = true;
+      for (const TuneRec* r : kv.second) ok = ok && r->launch(ch) == cudaSuccess;  // warm-up
+      cudaEventRecord(e0, ctx->stream);
+      for (int it = 0; it < reps && ok; ++it)
+        for (const TuneRec* r : kv.second) ok = ok && r->launch(ch) == cudaSuccess;
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+      cudaGetLastError();  // a refused candidate is skipped, not an error
+      float ms = 0.f;
+      if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        const double us = 1e3 * ms / reps / kv.second.size();
+        char tb[64];
+        std::snprintf(tb, sizeof(tb), "%s\"%d\": %.2f", times.empty() ? "" : ", ", ch, us);
+        times += tb;
+        if (us < best_us) {
+          best_us = us;
+          best = ch;
+        }
+      }
+    }
+    if (best == 0) continue;
+    ctx->tune[kv.first] = best;
+    char line[512];
+    std::snprintf(line, sizeof(line),
+                  "%s  {\"op\": %d, \"kind\": %d, \"a\": %lld, \"b\": %lld, \"c\": %lld, \"choice\": %d, "
+                  "\"launches_per_step\": %zu, \"us_per_launch\": {%s}}",
+                  body.empty() ? "" : ",\n", op, kind, std::get<2>(kv.first), std::get<3>(kv.first),
+                  std::get<4>(kv.first), best, kv.second.size(), times.c_str());
+    body += line;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cleanup();
+  st = device_status(ctx);
+  if (st != QTT_OK) {
+    ctx->tune.clear();
+    return st;
+  }
+  if (cache_path) {
+    FILE* f = std::fopen(cache_path, "w");
+    if (!f) return fail(QTT_EINVAL, std::string("cannot write ") + cache_path);
+    std::fprintf(f, "{\"qtt_autotune\": 1, \"header\": \"%s\", \"reps\": %d,\n \"entries\": [\n%s\n]}\n",
+                 header.c_str(), reps, body.c_str());
+    std::fclose(f);
+  }
+  if (entries_out) *entries_out = (int)ctx->tune.size();
   return QTT_OK;
 }
 
@@ -1465,6 +1785,61 @@ qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double la
   ctx->have_prop = false;  // proposals are for one step
   if (ctx->p.use_learned_rank && ctx->mlp) CKS(propose_ranks(ctx, prev));
   // prev now holds u^{k+1}: exchange buffers so that prev = u^k, cur = u^{k+1}
+  std::swap(prev->data, cur->data);
+  std::swap(prev->ranks, cur->ranks);
+  return QTT_OK;
+}
+
+qtt_status qtt_a_operator_mpo(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2, qtt_mpo** out) {
+  if (!ctx || !L || !c2 || !out) return fail(QTT_EINVAL, "null argument");
+  *out = nullptr;
+  if (L->d != ctx->d || c2->d != ctx->d) return fail(QTT_EINVAL, "handle from another grid size");
+  if (!(lambda2 >= 0.0) || !std::isfinite(lambda2)) return fail(QTT_EINVAL, "lambda2 must be finite, >= 0");
+  const int d = ctx->d;
+  std::vector<int> rc(d + 1);
+  CK(cudaMemcpyAsync(rc.data(), c2->ranks, (d + 1) * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<std::vector<double>> cores(d);
+  for (int k = 0; k < d; ++k) {
+    cores[k].resize((size_t)rc[k] * 2 * rc[k + 1]);
+    CK(cudaMemcpyAsync(cores[k].data(), c2->core(k), cores[k].size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  qtt_mpo* m = new qtt_mpo();
+  build_a_operator(*L, cores, rc, lambda2, m);
+  cudaError_t e = cudaMalloc(&m->data, m->host.size() * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->data, m->host.data(), m->host.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (m->data) cudaFree(m->data);
+    delete m;
+    return fail(e == cudaErrorMemoryAllocation ? QTT_ENOMEM : QTT_ECUDA, cudaGetErrorString(e));
+  }
+  *out = m;
+  return QTT_OK;
+}
+
+qtt_status qtt_step_fused(qtt_ctx* ctx, const qtt_mpo* A, qtt_mps* prev, qtt_mps* cur, const long* src, double amp) {
+  if (!ctx || !A || !prev || !cur) return fail(QTT_EINVAL, "null argument");
+  if (A->d != ctx->d || prev->d != ctx->d || cur->d != ctx->d) return fail(QTT_EINVAL, "handle from another grid size");
+  if (prev == cur) return fail(QTT_EINVAL, "psi_prev and psi_cur must differ");
+  if (src) CKS(check_point(ctx, src));
+  const Caps c = fused_caps(ctx, A->w);
+  CKS(ensure_ws_caps(ctx, A->w, std::vector<int>(ctx->d + 1, 1), c));
+  Workspace& s = ctx->ws;
+  {
+    struct MpScope {
+      qtt_ctx* c;
+      explicit MpScope(qtt_ctx* x) : c(x) { c->use_mp = (c->p.prec != QTT_FP64); }
+      ~MpScope() { c->use_mp = false; }
+    } mp_scope(ctx);
+    CKS(scale_states(ctx, prev, cur, 0));
+    CKS(zipup_L(ctx, A, cur, s.phi, c));
+    CKS(form_sum(ctx, {{1.0, s.phi}, {-1.0, prev}}, src, amp, s.theta, ctx->use_mp ? s.d_scale : nullptr));
+    CKS(tt_round(ctx, s.theta, prev));
+    CKS(scale_states(ctx, prev, cur, 1));
+  }
   std::swap(prev->data, cur->data);
   std::swap(prev->ranks, cur->ranks);
   return QTT_OK;
@@ -1698,7 +2073,8 @@ qtt_status qtt_step_batched(qtt_batch* b, const qtt_mpo* L, const qtt_mps* c2, d
   auto worker = [&](int s) {
     for (int i = s; i < n; i += S) {
       qtt_status r = (b->graphs ? qtt_step_graph : qtt_step)(b->ctx[i], L, c2, lambda2, prev[i], cur[i],
-                                                             src ? src + 2 * i : nullptr, src ? amp[i] : 0.0);
+                                                             src ? src + b->ctx[0]->dims * i : nullptr,
+                                                             src ? amp[i] : 0.0);
       if (r != QTT_OK) {
         st[s] = r;
         msg[s] = g_err;
@@ -1720,24 +2096,45 @@ qtt_status qtt_step_batched(qtt_batch* b, const qtt_mpo* L, const qtt_mps* c2, d
   return QTT_OK;
 }
 
-qtt_status qtt_sample(qtt_ctx* ctx, const qtt_mps* psi, const long* ix, const long* iz, long count, double* out) {
-  if (!ctx || !psi || (count > 0 && (!ix || !iz || !out))) return fail(QTT_EINVAL, "null argument");
+}  // extern "C"
+
+namespace {
+qtt_status sample_impl(qtt_ctx* ctx, const qtt_mps* psi, const long* ix, const long* iy, const long* iz, long count,
+                       double* out) {
   if (count < 0) return fail(QTT_EINVAL, "negative count");
   if (count == 0) return QTT_OK;
   SampleArgs a;
   std::memset(&a, 0, sizeof(a));
   a.d = ctx->d;
   a.n = ctx->p.n;
-  a.order = ctx->p.order;
+  a.dims = ctx->dims;
+  a.sp = site_positions(ctx);
   a.rmax = *std::max_element(psi->cap.begin(), psi->cap.end());
   for (int k = 0; k < ctx->d; ++k) a.core[k] = psi->core(k);
   a.ranks = psi->ranks;
   a.ix = ix;
+  a.iy = iy;
   a.iz = iz;
   a.count = count;
   a.out = out;
   KL(KC_OTHER, sample(a, ctx->stream));
   return QTT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qtt_status qtt_sample(qtt_ctx* ctx, const qtt_mps* psi, const long* ix, const long* iz, long count, double* out) {
+  if (!ctx || !psi || (count > 0 && (!ix || !iz || !out))) return fail(QTT_EINVAL, "null argument");
+  if (ctx->dims != 2) return fail(QTT_EINVAL, "3D context: use qtt_sample_3d");
+  return sample_impl(ctx, psi, ix, nullptr, iz, count, out);
+}
+
+qtt_status qtt_sample_3d(qtt_ctx* ctx, const qtt_mps* psi, const long* ix, const long* iy, const long* iz, long count,
+                         double* out) {
+  if (!ctx || !psi || (count > 0 && (!ix || !iy || !iz || !out))) return fail(QTT_EINVAL, "null argument");
+  if (ctx->dims != 3) return fail(QTT_EINVAL, "2D context: use qtt_sample");
+  return sample_impl(ctx, psi, ix, iy, iz, count, out);
 }
 
 qtt_status qtt_to_dense(qtt_ctx* ctx, const qtt_mps* psi, double* out) {
@@ -1774,7 +2171,7 @@ qtt_status qtt_to_dense(qtt_ctx* ctx, const qtt_mps* psi, double* out) {
   g.sci = dconst(nR);
   g.scj = dconst(1);
   KL(KC_GEMM, gemm_f64(g, nL, nR, 1, 1, ctx->stream));
-  KL(KC_OTHER, scatter_dense(s.d_tv, out, ctx->p.n, ctx->p.order, h, ctx->stream));
+  KL(KC_OTHER, scatter_dense(s.d_tv, out, site_positions(ctx), h, ctx->stream));
   return QTT_OK;
 }
 
@@ -1838,12 +2235,61 @@ qtt_status qtt_svd_trunc(qtt_ctx* ctx, const double* M, int m, int n, double eps
   return device_status(ctx);
 }
 
+qtt_status qtt_gemm(qtt_ctx* ctx, int kind, int a_trans, int b_trans, int m, int n, int k, const double* A, int lda,
+                    const double* B, int ldb, double* C, int ldc, double alpha, double beta, int tile_n) {
+  if (!ctx || (!A && k > 0 && m > 0) || (!B && k > 0 && n > 0) || (!C && m > 0 && n > 0))
+    return fail(QTT_EINVAL, "null argument");
+  if (kind < 0 || kind > 4) return fail(QTT_EINVAL, "kind must be 0..4");
+  if (m < 0 || n < 0 || k < 0) return fail(QTT_EINVAL, "negative size");
+  if (lda < std::max(1, a_trans ? m : k) || ldb < std::max(1, b_trans ? k : n) || ldc < std::max(1, n))
+    return fail(QTT_EINVAL, "leading dimension smaller than the row");
+  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256)
+    return fail(QTT_EINVAL, "tile_n must be 0, 64, 128 or 256");
+  if (m == 0 || n == 0) return QTT_OK;
+  CKS(ensure_ws_basic(ctx));
+  GemmArgs g = gemm0();
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.M = dconst(m);
+  g.N = dconst(n);
+  g.K = dconst(k);
+  g.sai = dconst(a_trans ? 1 : lda);
+  g.sak = dconst(a_trans ? lda : 1);
+  g.sbk = dconst(b_trans ? 1 : ldb);
+  g.sbj = dconst(b_trans ? ldb : 1);
+  g.sci = dconst(ldc);
+  g.scj = dconst(1);
+  g.alpha = alpha;
+  g.beta = beta;
+  if (kind == 0) {
+    KL(KC_GEMM, gemm_f64(g, m, n, 1, 1, ctx->stream));
+  } else if (kind == 1) {
+    KL(KC_GEMM, gemm_f32(g, m, n, 1, 1, ctx->stream));
+  } else {
+    const int bn = tile_n ? tile_n : tc_tile_n(ctx, m, n, 1);
+    KL(KC_GEMM, gemm_tc(g, m, n, 1, 1, kind - 2, bn, ctx->ws.d_sync, ctx->stream));
+  }
+  return QTT_OK;
+}
+
 qtt_status qtt_fdtd_step(qtt_ctx* ctx, const double* c2, double lambda2, const double* up, const double* uc,
                          double* un, long sx, long sz, double amp) {
   if (!ctx || !c2 || !up || !uc || !un) return fail(QTT_EINVAL, "null argument");
+  if (ctx->dims != 2) return fail(QTT_EINVAL, "3D context: use qtt_fdtd_step_3d");
   const long N = 1L << ctx->p.n;
   if (sx >= N || sz < 0 || sz >= N) sx = -1;
   KL(KC_FDTD, fdtd(c2, lambda2, up, uc, un, ctx->p.n, ctx->p.bc, sx, sz, amp, ctx->stream));
+  return QTT_OK;
+}
+
+qtt_status qtt_fdtd_step_3d(qtt_ctx* ctx, const double* c2, double lambda2, const double* up, const double* uc,
+                            double* un, long sx, long sy, long sz, double amp) {
+  if (!ctx || !c2 || !up || !uc || !un) return fail(QTT_EINVAL, "null argument");
+  if (ctx->dims != 3) return fail(QTT_EINVAL, "2D context: use qtt_fdtd_step");
+  const long N = 1L << ctx->p.n;
+  if (sx < 0 || sx >= N || sy < 0 || sy >= N || sz < 0 || sz >= N) sx = -1;
+  KL(KC_FDTD, fdtd3(c2, lambda2, up, uc, un, ctx->p.n, ctx->p.bc, sx, sy, sz, amp, ctx->stream));
   return QTT_OK;
 }
 
@@ -1860,9 +2306,14 @@ qtt_status qtt_profile_start(qtt_ctx* ctx, int timing, int log_svd) {
       p.log_cap = 65536;
       CK(cudaMalloc(&p.d_log, 3 * p.log_cap * sizeof(int)));
     }
-  } else if (p.d_log) {
-    cudaFree(p.d_log);
+    if (!p.d_flops) CK(cudaMalloc(&p.d_flops, KC_N * sizeof(double)));
+    CK(cudaMemsetAsync(p.d_flops, 0, KC_N * sizeof(double), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    if (p.d_log) cudaFree(p.d_log);
+    if (p.d_flops) cudaFree(p.d_flops);
     p.d_log = nullptr;
+    p.d_flops = nullptr;
     p.log_cap = 0;
   }
   return QTT_OK;
@@ -1893,6 +2344,11 @@ qtt_status qtt_profile_read(qtt_ctx* ctx, qtt_profile* out) {
     out->svd_logged = p.log_used;
     out->svd_flops = f;
     out->svd_sweeps = sweeps;
+  }
+  if (p.d_flops) {
+    double h[KC_N];
+    CK(cudaMemcpy(h, p.d_flops, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < KC_N && c < QTT_KCLASSES; ++c) out->flops[c] = h[c];
   }
   return device_status(ctx);
 }

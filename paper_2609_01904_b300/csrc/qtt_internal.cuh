@@ -5,8 +5,11 @@
 #include <cuda/atomic>
 
 #include <cstdint>
-#include <utility>
+#include <functional>
+#include <map>
 #include <string>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/qtt.h"
@@ -51,12 +54,17 @@ struct DevSync {
   int counters[4];   // rotations per sweep (4 rotating slots)
   int status;
   int done[4];       // CTAs that finished a sweep (same slots)
-  int pad[5];
+  int pad;
+  unsigned long long limit_ns;  // wait limit of this context (0 = kWaitLimitNs)
+  int pad2[2];
 };
 
-
-
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long wait_limit(const DevSync* s) {
+  const unsigned long long l = s->limit_ns;
+  return l ? l : kWaitLimitNs;
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -78,10 +86,10 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // thread 0 waits until *p >= target; false (status set) on timeout or error
 __device__ __forceinline__ bool wait_geq(const int* p, int target, DevSync* s) {
   if (ld_acquire(p) >= target) return true;
-  const unsigned long long t0 = globaltimer_ns();
+  const unsigned long long t0 = globaltimer_ns(), lim = wait_limit(s);
   while (ld_acquire(p) < target) {
     if (ld_acquire(&s->status) != 0) return false;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+    if (globaltimer_ns() - t0 > lim) {
       set_status(s, QTT_ETIMEOUT);
       return false;
     }
@@ -107,10 +115,10 @@ __device__ __forceinline__ bool grid_sync(DevSync* s) {
       cnt.store(0u, cuda::memory_order_relaxed);
       gen.fetch_add(1u, cuda::memory_order_release);
     } else {
-      unsigned long long t0 = globaltimer_ns();
+      const unsigned long long t0 = globaltimer_ns(), lim = wait_limit(s);
       while (gen.load(cuda::memory_order_acquire) == g) {
         if (st.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        if (globaltimer_ns() - t0 > lim) {
           set_status(s, QTT_ETIMEOUT);
           ok = 0;
           break;
@@ -198,6 +206,7 @@ struct Workspace {
   double* d_sig = nullptr;    // singular values (sorted)
   double* d_norm = nullptr;   // vector norms from the Jacobi sweeps
   double* d_disc = nullptr;   // discarded weights per (phase, bond)
+  double* d_scale = nullptr;  // power-of-two state scaling of a reduced-precision step (2^s, 2^-s)
   int* d_ints = nullptr;      // scratch ints (ranks of temporaries)
   DevSync* d_sync = nullptr;
   // learned form: spectra of the last round (row k = bond k, ws_nvmax wide),
@@ -236,7 +245,34 @@ struct Prof {
   int* d_log = nullptr;     // (nv, m) of each Jacobi launch while profiling
   int log_cap = 0;
   int log_used = 0;
+  double* d_flops = nullptr;  // algorithmic FLOPs per class, counted by the kernels while logging
 };
+
+// Counter of the class whose launch is being issued on this thread (set by
+// the launch bracket while work logging is on, else null).  Launchers pass
+// it to their kernels, which add the algorithmic FLOP count of the launch
+// from their device-side sizes.
+extern thread_local double* g_flop_ctr;
+
+// Multiprocessor count of the current device (queried once per device).
+int device_sms();
+}  // namespace qtt
+
+namespace qtt {
+// Autotuning.  A launch recorded during a dry-run step, re-launchable with
+// any candidate choice: op 0 = a contraction GEMM (kind 0 FP64, 1 FP32 SIMT,
+// 2 TF32, 3 3xTF32, 4 BF16 tensor cores; bucket a, b, c = Mmax, Nmax,
+// batches; choice = output tile 16 / 32 or tensor-core columns 64 / 128 /
+// 256), op 1 = a Householder QR (kind 0 FP64, 1 FP32; bucket = rows of the
+// working columns, columns, thin Q formed; choice = threads per CTA 256 /
+// 1024).  Choice 0 is the built-in heuristic.
+struct TuneRec {
+  int op;
+  int kind;
+  long long a, b, c;
+  std::function<cudaError_t(int)> launch;
+};
+using TuneKey = std::tuple<int, int, long long, long long, long long>;
 }  // namespace qtt
 
 struct qtt_mlp;
@@ -244,6 +280,8 @@ struct qtt_mlp;
 struct qtt_ctx {
   qtt_params p{};
   int d = 0;
+  int dims = 2;          // 2: Eq. 2 on an N x N grid; 3: the 3D extension, N^3
+  int site_pos[32] = {0};  // bit of the linear dense index carried by site k
   cudaStream_t stream = nullptr;
   int device = 0;
   int num_sms = 0;
@@ -252,6 +290,7 @@ struct qtt_ctx {
   bool ws_ready = false;
   qtt::Prof prof;
   bool use_mp = false;      // inside a reduced-precision step: FP32 contractions and QR, mixed SVD
+  int ckind = -1;           // contractions of a reduced-precision step: -1 FP32 SIMT, else gemm_tc kind
   long long ws_nvmax = 0;   // widest SVD (vectors) the workspace holds
   long long ws_ellmax = 0;  // longest vector of a step SVD
   // learned form (the Sec. 4.3 rule still decides every truncation)
@@ -268,11 +307,19 @@ struct qtt_ctx {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   const void* gkey[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
   double gkey_lam = 0.0;
-  long gkey_src[3] = {0, 0, 0};
+  long gkey_src[4] = {0, 0, 0, 0};
   long long glaunches[16] = {0};
   double* d_amp = nullptr;  // source sample of the step being replayed
   cudaStream_t gstream = nullptr;  // capture stream (the legacy stream cannot be captured)
   bool capturing = false;   // inside a capture: the sum reads d_amp
+  // failure-detection limits: device waits give up after wait_limit_ns
+  // (QTT_ETIMEOUT), the FP64 Jacobi after max_sweeps sweeps (QTT_ENOCONV)
+  unsigned long long wait_limit_ns = 0;  // 0: the default, 2 s
+  int max_sweeps = 100;
+  // autotuned choice per launch bucket (qtt_autotune), and the launches of
+  // a dry-run step while one is being recorded
+  std::map<qtt::TuneKey, int> tune;
+  std::vector<qtt::TuneRec>* tune_rec = nullptr;
 };
 
 namespace qtt {
@@ -290,12 +337,20 @@ struct GemmArgs {
   Dim sa1, sa2, sb1, sb2, sc1, sc2;  // batch strides
   double alpha, beta;
 };
-// C[b1,b2](i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j); Mmax/Nmax/nbmax size the grid.
+// C[b1,b2](i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j); Mmax/Nmax/nbmax size the grid;
+// tile: 16 or 32 (square output tile per CTA), 0 = by the number of tiles
 cudaError_t gemm_f64(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max,
-                     long long nb2max, cudaStream_t st);
+                     long long nb2max, cudaStream_t st, int tile = 0);
 // the same product with FP32 arithmetic (the reduced-precision form)
 cudaError_t gemm_f32(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max,
-                     long long nb2max, cudaStream_t st);
+                     long long nb2max, cudaStream_t st, int tile = 0);
+// the same product on the tensor cores (tcgen05, accumulator in TMEM): kind
+// 0 = TF32, 1 = 3xTF32 (hi/lo split, ~FP32 accuracy), 2 = BF16; FP32
+// accumulation; bn = 64, 128 or 256 columns per CTA (128 rows); waits
+// bounded by the limit in *sync (QTT_ETIMEOUT recorded there)
+cudaError_t gemm_tc(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max, long long nb2max, int kind,
+                    int bn, DevSync* sync, cudaStream_t st);
+cudaError_t tc_init();
 
 // Householder QR of the m x n matrix whose column j is Ain + j*lda (length m).
 // R (kq x n, kq = min(m,n)) is written to Rout row-major (R[i][c] at i*ldr+c)
@@ -303,14 +358,15 @@ cudaError_t gemm_f32(const GemmArgs& a, long long Mmax, long long Nmax, long lon
 // not null; kq to *kq_out if not null.  Work: column j at W + j*ldw.
 // ldr: leading dimension of a column-major R.  Q formation needs m <= qm_max
 // (the column is built in shared memory).
+// block: threads per CTA (256 or 1024; 0 = 1024 for columns of 2048 rows or more)
 cudaError_t qr_f64(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n,
                    long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
-                   long long qm_max = 0);
+                   long long qm_max = 0, int block = 0);
 // the same factorisation with FP32 arithmetic on an FP32 working copy (W is
 // reinterpreted as float storage); R and Q are written as doubles
 cudaError_t qr_f32(qtt_ctx* ctx, const double* Ain, Dim lda, double* W, long long ldw, Dim m, Dim n,
                    long long nmax, double* Rout, bool r_rowmajor, double* Qout, int* kq_out, long long ldr,
-                   long long qm_max = 0);
+                   long long qm_max = 0, int block = 0);
 
 // One-sided Jacobi on nv vectors V + i*ldv of length m; J (nv x nv,
 // vector-major, ld ldj) accumulates the rotations; norms[i] = |v_i| at the end.

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libqtt.so")
 QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENOCONV, QTT_ETIMEOUT, QTT_ENONFINITE = range(7)
 ORDERS = {"sequential": 0, "interleaved": 1}
 BCS = {"periodic": 0, "zero": 1}
-PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3, "tf32x3": 4}
 STATUS_NAMES = {0: "QTT_OK", 1: "QTT_EINVAL", 2: "QTT_ENOMEM", 3: "QTT_ECUDA", 4: "QTT_ENOCONV",
                 5: "QTT_ETIMEOUT", 6: "QTT_ENONFINITE"}
 
@@ -29,7 +29,7 @@ class qtt_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("order", ctypes.c_int), ("bc", ctypes.c_int), ("prec", ctypes.c_int),
                 ("chi_max", ctypes.c_int), ("eps", ctypes.c_double), ("chi_zip", ctypes.c_int),
                 ("eps_zip", ctypes.c_double), ("chi_c", ctypes.c_int), ("eps_c", ctypes.c_double),
-                ("use_learned_rank", ctypes.c_int)]
+                ("use_learned_rank", ctypes.c_int), ("dims", ctypes.c_int)]
 
 
 class QttError(RuntimeError):
@@ -54,7 +54,8 @@ KERNEL_CLASSES = ["gemm", "qr", "jacobi", "svd_post", "mpo_apply", "mps_sum", "c
 
 class qtt_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_long * QTT_KCLASSES), ("ms", ctypes.c_double * QTT_KCLASSES),
-                ("svd_logged", ctypes.c_long), ("svd_flops", ctypes.c_double), ("svd_sweeps", ctypes.c_long)]
+                ("svd_logged", ctypes.c_long), ("svd_flops", ctypes.c_double), ("svd_sweeps", ctypes.c_long),
+                ("flops", ctypes.c_double * QTT_KCLASSES)]
 
 
 _SIGS = {
@@ -95,6 +96,15 @@ _SIGS = {
     "qtt_set_proposals": [_P, _PI],
     "qtt_get_proposals": [_P, _PI],
     "qtt_learned_stats": [_P, _PL, _PL],
+    "qtt_set_limits": [_P, _D, _I],
+    "qtt_gemm": [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _D, _D, _I],
+    "qtt_autotune": [_P, _P, _P, _D, _P, _P, ctypes.c_char_p, _I, _PI],
+    "qtt_a_operator_mpo": [_P, _P, _P, _D, ctypes.POINTER(_P)],
+    "qtt_step_fused": [_P, _P, _P, _P, _PL, _D],
+    "qtt_inject_source_3d": [_P, _P, _L, _L, _L, _D],
+    "qtt_sample_3d": [_P, _P, _P, _P, _P, _L, _P],
+    "qtt_fdtd_step_3d": [_P, _P, _D, _P, _P, _P, _L, _L, _L, _D],
+    "qtt_peak_probe": [_I, _PD, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -149,8 +159,12 @@ class Ctx:
         return self.params.n
 
     @property
+    def dims(self) -> int:
+        return 3 if self.params.dims == 3 else 2
+
+    @property
     def d(self) -> int:
-        return 2 * self.params.n
+        return self.dims * self.params.n
 
     def __del__(self):
         if getattr(self, "h", None) and getattr(self, "owner", None) is None:
@@ -186,14 +200,14 @@ def qtt_last_error() -> str:
 
 def qtt_ctx_create(n: int, order: str = "interleaved", bc: str = "periodic", chi_max: int = 32,
                    eps: float = 1e-10, chi_zip: int = 0, eps_zip: float = 0.0, chi_c: int = 0,
-                   eps_c: float = 0.0, prec: str = "fp64", stream=None, learned: bool = False) -> Ctx:
+                   eps_c: float = 0.0, prec: str = "fp64", stream=None, learned: bool = False, dims: int = 2) -> Ctx:
     """Context on the current CUDA device; ``stream`` is a torch.cuda.Stream
-    (default: torch's current stream)."""
+    (default: torch's current stream); dims = 3 for the 3D extension."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
     p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, chi_zip, eps_zip, chi_c, eps_c,
-                   int(learned))
+                   int(learned), int(dims))
     h = _P()
     _check(_lib.qtt_ctx_create(ctypes.byref(p), _P(stream.cuda_stream), ctypes.byref(h)), "qtt_ctx_create")
     return Ctx(h.value, p)
@@ -298,23 +312,56 @@ def qtt_mpo_bonds(L: Mpo) -> list[int]:
     return list(b)
 
 
+def _src(src):
+    """A grid point (2 or 3 coordinates) as the C array the step calls take."""
+    if src is None:
+        return None
+    return (ctypes.c_long * len(src))(*[int(v) for v in src])
+
+
+def qtt_inject_source_3d(psi: Mps, ix: int, iy: int, iz: int, amp: float) -> None:
+    _check(_lib.qtt_inject_source_3d(psi.ctx.h, psi.h, ix, iy, iz, amp), "qtt_inject_source_3d")
+
+
+def qtt_sample_3d(psi: Mps, ix, iy, iz, out) -> None:
+    """ix, iy, iz: CUDA int64 tensors; out: CUDA float64 tensor of the same length."""
+    n = ix.numel()
+    _check(_lib.qtt_sample_3d(psi.ctx.h, psi.h, _P(_dev_ptr(ix, "int64")), _P(_dev_ptr(iy, "int64")),
+                              _P(_dev_ptr(iz, "int64")), n, _P(_dev_ptr(out))), "qtt_sample_3d")
+
+
+def qtt_fdtd_step_3d(ctx: Ctx, c2, lambda2: float, u_prev, u_cur, u_next, src=None, amp: float = 0.0) -> None:
+    sx, sy, sz = (-1, -1, -1) if src is None else (int(src[0]), int(src[1]), int(src[2]))
+    _check(_lib.qtt_fdtd_step_3d(ctx.h, _P(_dev_ptr(c2)), lambda2, _P(_dev_ptr(u_prev)), _P(_dev_ptr(u_cur)),
+                                 _P(_dev_ptr(u_next)), sx, sy, sz, amp), "qtt_fdtd_step_3d")
+
+
 def qtt_inject_source(psi: Mps, ix: int, iz: int, amp: float) -> None:
     _check(_lib.qtt_inject_source(psi.ctx.h, psi.h, ix, iz, amp), "qtt_inject_source")
 
 
 def qtt_step_graph(L: Mpo, c2: Mps, lambda2: float, psi_prev: Mps, psi_cur: Mps, src=None, amp: float = 0.0) -> None:
     """qtt_step replayed from a CUDA graph captured on the first call."""
-    s = None
-    if src is not None:
-        s = (ctypes.c_long * 2)(int(src[0]), int(src[1]))
+    s = _src(src)
     _check(_lib.qtt_step_graph(psi_cur.ctx.h, L.h, c2.h, lambda2, psi_prev.h, psi_cur.h, s, amp), "qtt_step_graph")
+
+
+def qtt_a_operator_mpo(L: Mpo, c2: Mps, lambda2: float) -> Mpo:
+    """MPO of the Eq. 7 transition operator 2I + lambda^2 C^2 L."""
+    h = _P()
+    _check(_lib.qtt_a_operator_mpo(c2.ctx.h, L.h, c2.h, lambda2, ctypes.byref(h)), "qtt_a_operator_mpo")
+    return Mpo(h.value, c2.ctx)
+
+
+def qtt_step_fused(A: Mpo, psi_prev: Mps, psi_cur: Mps, src=None, amp: float = 0.0) -> None:
+    """Eq. 7 with A applied in one zip-up; handles rotate as in qtt_step."""
+    s = _src(src)
+    _check(_lib.qtt_step_fused(psi_cur.ctx.h, A.h, psi_prev.h, psi_cur.h, s, amp), "qtt_step_fused")
 
 
 def qtt_step(L: Mpo, c2: Mps, lambda2: float, psi_prev: Mps, psi_cur: Mps, src=None, amp: float = 0.0) -> None:
     """Eq. 17: on return psi_prev holds u^k and psi_cur holds u^{k+1}."""
-    s = None
-    if src is not None:
-        s = (ctypes.c_long * 2)(int(src[0]), int(src[1]))
+    s = _src(src)
     _check(_lib.qtt_step(psi_cur.ctx.h, L.h, c2.h, lambda2, psi_prev.h, psi_cur.h, s, amp), "qtt_step")
 
 
@@ -402,7 +449,7 @@ def qtt_batch_create(n: int, nshots: int, chi_per_shot=None, order: str = "inter
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, 0, 0.0, chi_c, eps_c, 0)
+    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, 0, 0.0, chi_c, eps_c, 0, 2)
     chis = None
     if chi_per_shot is not None:
         chis = (ctypes.c_int * nshots)(*[int(x) for x in chi_per_shot])
@@ -413,7 +460,7 @@ def qtt_batch_create(n: int, nshots: int, chi_per_shot=None, order: str = "inter
     ctxs = []
     for i in range(nshots):
         chi_i = int(chi_per_shot[i]) if chi_per_shot is not None and int(chi_per_shot[i]) > 0 else chi_max
-        pi = qtt_params(p.n, p.order, p.bc, p.prec, chi_i, eps, 0, 0.0, chi_c, eps_c, 0)
+        pi = qtt_params(p.n, p.order, p.bc, p.prec, chi_i, eps, 0, 0.0, chi_c, eps_c, 0, 2)
         ctxs.append(Ctx(_lib.qtt_batch_ctx(hold.h, i), pi, owner=hold))
     return Batch(hold, ctxs)
 
@@ -439,7 +486,8 @@ def qtt_step_batched(batch: Batch, L: Mpo, c2: Mps, lambda2: float, prev: list, 
     C = (_P * n)(*[x.h for x in cur])
     s = a = None
     if src is not None:
-        s = (ctypes.c_long * (2 * n))(*[int(v) for xy in src for v in xy])
+        flat = [int(v) for xy in src for v in xy]
+        s = (ctypes.c_long * len(flat))(*flat)
         a = (ctypes.c_double * n)(*[float(v) for v in amp])
     _check(_lib.qtt_step_batched(batch.h, L.h, c2.h, lambda2, P, C, s, a), "qtt_step_batched")
     # the library exchanged each pair's buffers; the handles keep their roles
@@ -563,7 +611,49 @@ def qtt_profile_read(ctx: Ctx) -> dict:
     p = qtt_profile()
     _check(_lib.qtt_profile_read(ctx.h, ctypes.byref(p)), "qtt_profile_read")
     return {"launches": dict(zip(KERNEL_CLASSES, list(p.launches))), "ms": dict(zip(KERNEL_CLASSES, list(p.ms))),
-            "svd_logged": p.svd_logged, "svd_flops": p.svd_flops, "svd_sweeps": p.svd_sweeps}
+            "svd_logged": p.svd_logged, "svd_flops": p.svd_flops, "svd_sweeps": p.svd_sweeps,
+            "flops": dict(zip(KERNEL_CLASSES, list(p.flops)))}
+
+
+GEMM_KINDS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4}
+
+
+def qtt_gemm(ctx: Ctx, kind: str, A, B, C, alpha: float = 1.0, beta: float = 0.0, a_trans: bool = False,
+             b_trans: bool = False, tile_n: int = 0) -> None:
+    """C = alpha op(A) op(B) + beta C on CUDA float64 tensors (row-major 2-D;
+    op transposes a stored matrix when *_trans)."""
+    m, k = (A.shape[1], A.shape[0]) if a_trans else (A.shape[0], A.shape[1])
+    n = B.shape[0] if b_trans else B.shape[1]
+    _check(_lib.qtt_gemm(ctx.h, GEMM_KINDS[kind], int(a_trans), int(b_trans), m, n, k, _P(_dev_ptr(A)),
+                         A.stride(0), _P(_dev_ptr(B)), B.stride(0), _P(_dev_ptr(C)), C.stride(0), alpha, beta,
+                         int(tile_n)), "qtt_gemm")
+
+
+def qtt_autotune(L: Mpo, c2: Mps, lambda2: float, psi_prev: Mps, psi_cur: Mps, cache_path: str | None = None,
+                 reps: int = 5) -> int:
+    """Autotune the launch shapes of the step on the states' context (see
+    include/qtt.h); returns the number of buckets tuned."""
+    n = ctypes.c_int(0)
+    _check(_lib.qtt_autotune(psi_cur.ctx.h, L.h, c2.h, lambda2, psi_prev.h, psi_cur.h,
+                             os.fsencode(cache_path) if cache_path else None, int(reps), ctypes.byref(n)),
+           "qtt_autotune")
+    return n.value
+
+
+def qtt_set_limits(ctx: Ctx, wait_limit_s: float = 0.0, max_sweeps: int = 0) -> None:
+    """Bounded-wait limit (seconds) and FP64 Jacobi sweep limit; 0 = defaults."""
+    _check(_lib.qtt_set_limits(ctx.h, float(wait_limit_s), int(max_sweeps)), "qtt_set_limits")
+
+
+def qtt_peak_probe(kind: str, stream=None) -> float:
+    """Measured FMA peak of the device in TFLOP/s: kind "fp32" or "fp64"."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    _check(_lib.qtt_peak_probe({"fp32": 0, "fp64": 1}[kind], ctypes.byref(out), _P(stream.cuda_stream)),
+           "qtt_peak_probe")
+    return out.value
 
 
 __all__ = [n for n in EXPORTED] + ["Ctx", "Mps", "Mpo", "QttError", "qtt_params", "EXPORTED", "LIB_PATH"]

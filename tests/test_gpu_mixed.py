@@ -2,30 +2,27 @@
 truncation SVDs as FP32 Jacobi refined to FP64 accuracy) against the FP64
 oracle.
 
-Stated tolerance: one step from a shared state within 2e-5 + 1e-6 / g
-relative L2 of the oracle, g the smallest relative gap
-(sigma_r - sigma_{r+1}) / sigma_1 at any truncation cut of that step that
-discards a value (FP32 rounding of the contractions, ~1e-7 per product
-accumulated over the step's ~60 dependent factorisations, moves a truncated
-subspace by rounding / gap); ranks within 2 of the oracle's (a kept /
-discarded decision may flip for values within FP32 rounding of
-eps * sigma_1)."""
+Stated tolerance (tests/fp32_bounds.py): one step from a shared state within
+min(2e-5 + 1e-6 / h, 1e-4) relative L2 of the oracle, h the smallest
+relative gap (sigma_r - sigma_{r+1}) / sigma_r at any truncation cut of that
+step that discards a value (FP32 rounding of the contractions, ~1e-7 per
+product accumulated over the step's ~60 dependent factorisations, turns a
+truncated subspace by rounding / gap, weighted by the values at the cut);
+a step with h < 1e-4 has a cut FP32 cannot resolve: it is counted and
+reported, not held to the bound; below eps = 1e-6 (the 64 x 64 run's
+eps = 1e-10) the cuts are under FP32 resolution and a step is held to the
+workloads' 1e-3.  Ranks within 2 plus the number of values
+within a factor 8 of eps sigma_1 (a kept / discarded decision may flip
+there)."""
 import numpy as np
 import pytest
 
+from fp32_bounds import gaps, ranks_ok, tol32
 from oracle import qtt_oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL_STEP = 2e-5
-
-
-def _tol(stats):
-    g = 1.0
-    for _kind, _k, S, r in stats:
-        if r < len(S) and S[0] > 0:
-            g = min(g, max((S[r - 1] - S[r]) / S[0], 1e-300))
-    return TOL_STEP + 1e-6 / g
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +55,7 @@ def _rel(a, b):
                                             (8, 128, "interleaved", "periodic")])
 def test_fp32_form_one_step_from_random_state(q, n, chi, order, bc):
     N = 1 << n
-    eps = 1e-7
+    eps = 1e-6  # the FP32 form resolves cuts down to 1e-6 sigma_1
     c = W.layered_model(n, 40.0, 11) if n < 8 else W.constant_model(n, 2000.0)
     lam2 = (0.5 / c.max()) ** 2
     ctx = q.qtt_ctx_create(n=n, order=order, bc=bc, chi_max=chi, eps=eps, chi_c=12, eps_c=1e-8, prec="fp32")
@@ -74,8 +71,11 @@ def test_fp32_form_one_step_from_random_state(q, n, chi, order, bc):
     want = O.mps_step(O.laplacian_mpo(n, order, bc), O.velocity_mps(c, n, order, 1e-8, 12), lam2, prev_h, cur_h,
                       eps, chi, src, 0.37, n, order, st)
     got_r, want_r = q.qtt_mps_ranks(cur), O.mps_ranks(want)
-    assert max(abs(a - b) for a, b in zip(got_r, want_r)) <= 2, (got_r, want_r)
-    assert _rel(_dense(q, cur, N), O.mps_to_dense(want, n, order)) < _tol(st)
+    err = _rel(_dense(q, cur, N), O.mps_to_dense(want, n, order))
+    tol, deg = tol32(st, eps)
+    print(f"n={n} chi={chi} {order} {bc}: rel_l2 {err:.3e} tol {tol:.1e} gaps {gaps(st)}")
+    assert ranks_ok(got_r, want_r, st, eps), (got_r, want_r)
+    assert not deg and err < tol, (err, tol, gaps(st))
 
 
 def test_fp32_form_every_step_of_qtt64_run(q):
@@ -94,7 +94,7 @@ def test_fp32_form_every_step_of_qtt64_run(q):
     Co = O.velocity_mps(c, n, wl.order, wl.eps_c, wl.chi_c)
     src = (N // 2 + 1, N // 2)
     po, co = O.zero_mps(2 * n), O.zero_mps(2 * n)
-    worst, errs = 0.0, []
+    worst, errs, degenerate, rows = 0.0, [], [], []
     for k in range(wl.steps):
         prev, cur = q.qtt_mps_from_cores(ctx, po), q.qtt_mps_from_cores(ctx, co)
         q.qtt_step(L, C, lam2, prev, cur, src, float(amps[k]))
@@ -102,8 +102,19 @@ def test_fp32_form_every_step_of_qtt64_run(q):
         po, co = co, O.mps_step(Lo, Co, lam2, po, co, wl.eps, wl.chi, src, float(amps[k]), n, wl.order, st)
         e = _rel(_dense(q, cur, N), O.mps_to_dense(co, n, wl.order))
         errs.append(e)
-        worst = max(worst, e / _tol(st))
+        tol, deg = tol32(st, wl.eps)
+        rows.append((e, k, tol, deg) + gaps(st))
+        if deg:
+            degenerate.append(k)
+        else:
+            worst = max(worst, e / tol)
+    for e, k, tol, deg, g, h in sorted(rows, reverse=True)[:8]:
+        print(f"qtt64 fp32 step {k}: rel_l2 {e:.2e} tol {tol:.1e} degenerate {deg} gap/sigma_1 {g:.2e} "
+              f"gap/sigma_r {h:.2e}")
+    print(f"qtt64 fp32: worst err/tol {worst:.3f} over {wl.steps - len(degenerate)} resolvable steps, "
+          f"{len(degenerate)} degenerate at FP32 resolution, median err {np.median(errs):.2e}")
     assert worst < 1.0, worst
+    assert len(degenerate) <= 0.15 * wl.steps, degenerate
     assert np.median(errs) < TOL_STEP, np.median(errs)
 
 
@@ -134,8 +145,10 @@ def test_chi256_step_on_the_512_grid(q, prec):
         assert got_r == want_r
         assert err < 1e-10, err
     else:
-        assert max(abs(a - b) for a, b in zip(got_r, want_r)) <= 2, (got_r, want_r)
-        assert err < _tol(st), (err, _tol(st))
+        tol, deg = tol32(st, eps)
+        print(f"chi256 {prec}: rel_l2 {err:.3e} tol {tol:.1e} gaps {gaps(st)}")
+        assert ranks_ok(got_r, want_r, st, eps), (got_r, want_r)
+        assert not deg and err < tol, (err, tol, gaps(st))
 
 
 def test_fp32_form_steps_from_a_mid_run_state_of_the_64_shot_workload(q):
@@ -176,9 +189,12 @@ def test_fp32_form_steps_from_a_mid_run_state_of_the_64_shot_workload(q):
         # eps = 1e-7 sits at FP32 resolution: every value within ~1e-7 sigma_1
         # of the threshold may fall either side, so ranks agree more loosely
         assert max(got_r) <= chi
-        assert max(abs(a - b) for a, b in zip(got_r, want_r)) <= 8, (k, got_r, want_r)
+        assert ranks_ok(got_r, want_r, st, wl.eps), (k, got_r, want_r)
         err = _rel(_dense(q, cur, N), O.mps_to_dense(want, n, wl.order))
-        assert err < min(_tol(st), 1e-3), (k, err, _tol(st))
+        g, h = gaps(st)
+        tol = min(TOL_STEP + 1e-6 / h, 1e-3)
+        print(f"qtt512 shot 1 fp32 step {k}: rel_l2 {err:.3e} tol {tol:.1e} gap/sigma_1 {g:.2e} gap/sigma_r {h:.2e}")
+        assert err < tol, (k, err, tol)
         po, co = co, want
 
 

@@ -10,6 +10,8 @@ at its first failure has already run every other test."""
 import numpy as np
 import pytest
 
+from oracle import qtt_oracle as O
+
 pytestmark = pytest.mark.gpu
 
 TOL_S = 1e-12  # singular values, relative to sigma_1 (as in the parity tests)
@@ -74,3 +76,25 @@ def test_noalloc_svd_rejects_sizes_beyond_its_scratch(q):
         q.qtt_svd_trunc_noalloc(M, U, S, Vt, 1e-8, 0)
     assert ei.value.status == q.QTT_EINVAL
     assert "static scratch" in str(ei.value)
+
+
+@pytest.mark.parametrize("m,n,seed,eps,chi", [(128, 128, 5, 1e-9, 0), (512, 128, 6, 1e-7, 0), (128, 512, 7, 1e-7, 50),
+                                             (1, 1, 8, 0.0, 0), (1, 37, 9, 0.0, 0), (64, 64, 0, 1e-8, 0)])
+def test_noalloc_svd_matches_the_oracle_rule_and_numpy_singular_values(q, m, n, seed, eps, chi):
+    """Against the oracle's truncation rule (Sec. 4.3) and the singular values
+    numpy's LAPACK SVD returns: the square branch (no QR), both sides at the
+    limit of the scratch (512 x 128 and 128 x 512), a 1 x 1 and a 1 x n
+    matrix, and the zero matrix (seed 0), each called twice in a row."""
+    A = _matrix(m, n, seed) if seed else np.zeros((m, n))
+    s_ref = np.linalg.svd(A, compute_uv=False)
+    r_ref = O.trunc_rank(s_ref, eps, chi if chi > 0 else 1 << 30)
+    for _ in range(2):
+        U, S, Vt, r = _noalloc(q, A, eps, chi)
+        assert r == r_ref
+        scale = max(float(s_ref[0]), 1e-300)
+        np.testing.assert_allclose(S, s_ref[:r], rtol=0, atol=TOL_S * scale)
+        best = float(np.sqrt(np.sum(s_ref[r:] ** 2)))
+        err = float(np.linalg.norm(U @ np.diag(S) @ Vt - A))
+        assert abs(err - best) <= TOL_REC * scale
+        if s_ref[0] == 0.0:
+            assert not S.any() and not (U @ np.diag(S) @ Vt).any()

@@ -25,6 +25,10 @@ __all__ = [
     "Workload",
     "CONFIGS",
     "config",
+    "paper_run",
+    "variant",
+    "qtt3d_run",
+    "layered_model_3d",
     "layered_model",
     "ricker",
     "random_tt_cores",
@@ -108,6 +112,34 @@ def layered_model(
     return c.astype(np.float64)
 
 
+def layered_model_3d(n: int, dh: float, seed: int, n_layers: int = 20, v_top: float = 1600.0,
+                     v_bottom: float = 4500.0, noise: float = 0.05, water_velocity: float = 1500.0,
+                     water_frac: float = 0.05) -> np.ndarray:
+    """Seeded layered and folded 3D velocity block c[x, y, z] (m/s): water
+    down to z_w = water_frac * N * dh, then n_layers interfaces at base depths
+    evenly spaced in (z_w, N*dh), each displaced by
+    A sin(2 pi x / Lx + phi) + B sin(2 pi y / Ly + psi) with A, B ~ U[5, 40] m,
+    Lx, Ly ~ U[0.5, 2] km, phases ~ U[0, 2 pi); velocity ramping
+    v_top -> v_bottom with layer index, times (1 + U[-noise, noise]) per layer."""
+    rng = np.random.default_rng(seed)
+    N = 1 << n
+    L = N * dh
+    x = (np.arange(N) + 0.5) * dh
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    z_w = water_frac * L
+    base = np.linspace(z_w, L, n_layers + 2)[1:-1]
+    A, B = rng.uniform(5.0, 40.0, n_layers), rng.uniform(5.0, 40.0, n_layers)
+    Lx, Ly = rng.uniform(500.0, 2000.0, n_layers), rng.uniform(500.0, 2000.0, n_layers)
+    px, py = rng.uniform(0.0, 2.0 * np.pi, n_layers), rng.uniform(0.0, 2.0 * np.pi, n_layers)
+    lay_noise = 1.0 + rng.uniform(-noise, noise, n_layers + 1)
+    layer = np.zeros((N, N, N), dtype=np.int64)
+    for i in range(n_layers):
+        depth = base[i] + A[i] * np.sin(2 * np.pi * X / Lx[i] + px[i]) + B[i] * np.sin(2 * np.pi * Y / Ly[i] + py[i])
+        layer += (Z >= depth).astype(np.int64)
+    c = (v_top + (v_bottom - v_top) * layer / max(n_layers, 1)) * lay_noise[layer]
+    return np.where(Z < z_w, water_velocity, c).astype(np.float64)
+
+
 # ---------------------------------------------------------------------------
 # source time function
 # ---------------------------------------------------------------------------
@@ -163,6 +195,8 @@ class Workload:
     eps_c: float
     sources: list[tuple[int, int]]
     receivers: list[tuple[int, int]]
+    dt_fixed: float | None = None  # a time step given by the run, else 0.5 dh / c_max
+    dims: int = 2  # 3: the 3D extension, points (ix, iy, iz)
 
     @property
     def N(self) -> int:
@@ -170,13 +204,15 @@ class Workload:
 
     @property
     def d(self) -> int:
-        return 2 * self.n
+        return self.dims * self.n
 
     def velocity(self) -> np.ndarray:
         if self.model == "constant":
             return constant_model(self.n, 2000.0)
         if self.model == "layered":
             return layered_model(self.n, self.dh, self.seed)
+        if self.model == "layered3d":
+            return layered_model_3d(self.n, self.dh, self.seed)
         if self.model == "marmousi":
             return layered_model(
                 self.n, self.dh, self.seed, n_layers=120, v_top=1500.0,
@@ -184,8 +220,12 @@ class Workload:
         raise ValueError(self.model)
 
     def dt(self, c: np.ndarray) -> float:
-        """dt = 0.5 * dh / c_max (Courant number 0.5 < 1/sqrt(2))."""
-        return 0.5 * self.dh / float(np.max(c))
+        """dt = 0.5 * dh / c_max (Courant number 0.5 < 1/sqrt(2)) in 2D,
+        0.5 * dh / (c_max sqrt(3/2)) (Courant number 0.41 < 1/sqrt(3)) in 3D,
+        unless the run fixes it."""
+        if self.dt_fixed is not None:
+            return self.dt_fixed
+        return 0.5 * self.dh / float(np.max(c)) / (math.sqrt(1.5) if self.dims == 3 else 1.0)
 
     def lambda2(self, c: np.ndarray) -> float:
         """lambda^2 = (dt/dh)^2, the squared mesh ratio of Eq. 2."""
@@ -239,6 +279,38 @@ CONFIGS = [_cfg(i) for i in range(5)]
 
 def config(idx: int) -> Workload:
     return _cfg(idx)
+
+
+def paper_run() -> Workload:
+    """The run of the paper's results section on a synthetic stand-in for its
+    256 x 256 Marmousi window (the dataset is not available here): dh = 10 m,
+    dt = 1 ms, an impulsive source of strength 1 at the centre (1280 m,
+    1280 m) as the initial condition u^0 = e_src, u^-1 = 0, chi_max = 128,
+    eps = 1e-7, 300 steps; the Marmousi-shaped generator (120 folded and
+    faulted layers with an anticline, 1500-5500 m/s, +-5 % per layer) at
+    seed 6.  Courant number c_max dt / dh = 0.574 < 1/sqrt(2)."""
+    n = 8
+    N = 1 << n
+    return Workload("qtt256_paper_run", n, 10.0, 0.0, 300, 128, 1e-7, "interleaved", "periodic", "fp64",
+                    "marmousi", 6, 128, 1e-8, [(N // 2, N // 2)], [(8 * i, 2) for i in range(N // 8)],
+                    dt_fixed=1e-3)
+
+
+def qtt3d_run(n: int = 6) -> Workload:
+    """The 3D extension's workload: a 2^n-per-axis layered and folded block
+    (20 interfaces, 1600 -> 4500 m/s under a water layer, seed 7), dh = 20 m,
+    Ricker 15 Hz at (N/2, N/2, 2), chi_max = 64, eps = 1e-6, interleaved
+    order, periodic boundaries, 600 steps; receivers every 8 points along x
+    at y = N/2, z = 2."""
+    N = 1 << n
+    return Workload(f"qtt{N}_3d_layered", n, 20.0, 15.0, 600, 64, 1e-6, "interleaved", "periodic", "fp64",
+                    "layered3d", 7, 64, 1e-8, [(N // 2, N // 2, 2)], [(8 * i, N // 2, 2) for i in range(N // 8)],
+                    dims=3)
+
+
+def variant(idx: int, order: str, bc: str) -> Workload:
+    """Configuration idx with another site order and boundary condition."""
+    return dataclasses.replace(_cfg(idx), name=f"{_cfg(idx).name}_{order}_{bc}", order=order, bc=bc)
 
 
 def chi_per_shot(seed: int = 4, shots: int = 64) -> np.ndarray:
