@@ -740,7 +740,7 @@ def run_3d(args):
     c = wl.velocity()
     lam2 = wl.lambda2(c)
     N = wl.N
-    mid = wl.steps // 2
+    mid = wl.steps // 4
     nst = args.err_steps
     amps = wl.source_amplitudes(c, mid + args.warmup + args.steps + nst + 2)
     src = wl.sources[0]
@@ -762,6 +762,10 @@ def run_3d(args):
                 q.qtt_fdtd_step_3d(ctx, c2, lam2, up, uc, un, src, float(amps[k]))
                 up, uc, un = uc, un, up
             prev, cur = q.qtt_mps_from_dense(ctx, up), q.qtt_mps_from_dense(ctx, uc)
+            comp = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+            q.qtt_to_dense(cur, comp)
+        q.qtt_ctx_sync(ctx)
+        comp_err = float(torch.linalg.norm(comp - uc) / torch.linalg.norm(uc))
         step = q.qtt_step_graph if args.graph else q.qtt_step
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
         with torch.cuda.stream(stream):
@@ -780,7 +784,7 @@ def run_3d(args):
         fields["fdtd"] = uc.cpu().numpy()
         out[form] = {"ms_per_step": round(float(np.median(t)), 3), "steps_per_s": 1e3 / float(np.median(t)),
                      "ranks_end": q.qtt_mps_ranks(cur), "c2_ranks": q.qtt_mps_ranks(C),
-                     "mpo_bonds": q.qtt_mpo_bonds(L)}
+                     "mpo_bonds": q.qtt_mpo_bonds(L), "start_state_compression_rel_l2": comp_err}
         del C, L, prev, cur, ctx
     rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
     for form in out:
@@ -906,6 +910,50 @@ def run_learned(args):
             "field_rel_l2_learned_vs_plain": rel(fields["learned"], fields["plain"]),
             "field_rel_l2_vs_dense_fdtd": {m: rel(fields[m], fd) for m in fields},
             "speedup_learned_vs_plain": res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"]}
+
+
+def run_gemm(args):
+    """The contraction kernel on its own (qtt_gemm): achieved TFLOP/s of each
+    operand form on square GEMMs of FP64 operands in HBM (inputs of 3 x 8 m^2
+    bytes, larger than L2 from m = 2048), against the measured peak of the
+    pipe it runs on (tensor-core forms: the bf16 peak of MEASURED_PEAKS.json,
+    tf32 = bf16 / 2 nominal; 3xTF32 counts its three products as useful work
+    of 2 m^3 flops only)."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    stream = torch.cuda.Stream()
+    ctx = q.qtt_ctx_create(n=6, chi_max=32, stream=stream)
+    peaks = measured_peaks(q, stream)
+    out = {}
+    for m in (1024, 4096):
+        A = torch.randn((m, m), dtype=torch.float64, device="cuda")
+        B = torch.randn((m, m), dtype=torch.float64, device="cuda")
+        C = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+        for kind in ("fp64", "fp32", "tf32", "tf32x3", "bf16"):
+            if kind == "fp64" and m > 2048:
+                continue
+            best = None
+            for tile in ((0,) if kind in ("fp64", "fp32") else (128, 256)):
+                with torch.cuda.stream(stream):
+                    q.qtt_gemm(ctx, kind, A, B, C, tile_n=tile)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(3):
+                        q.qtt_gemm(ctx, kind, A, B, C, tile_n=tile)
+                    e1.record(stream)
+                q.qtt_ctx_sync(ctx)
+                ms = e0.elapsed_time(e1) / 3
+                tf = 2.0 * m ** 3 / (ms * 1e-3) / 1e12
+                if best is None or tf > best[0]:
+                    best = (tf, ms, tile)
+            pipe = {"fp64": "fp64", "fp32": "fp32", "tf32": "tf32", "tf32x3": "tf32", "bf16": "bf16"}[kind]
+            peak = peaks.get(f"{pipe}_tflops")
+            out[f"{kind}/m={m}"] = {"tflops": best[0], "ms": round(best[1], 3), "tile_n": best[2], "pipe": pipe,
+                                    "peak_tflops": peak, "frac": best[0] / peak if peak else None}
+    return {"metric": "contraction kernel TFLOP/s per operand form (square GEMMs, FP64 operands in HBM)",
+            "unit": "TFLOP/s", "value": out["tf32/m=4096"]["tflops"], "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic (standard normal matrices)", "config": {"workload": "gemm", "m": [1024, 4096]},
+            "peaks": peaks, "kernels": out}
 
 
 def compare_forms(q, wl, c, amps, args):
@@ -1065,7 +1113,7 @@ def main():
     ap.add_argument("--graph", type=int, default=1, help="1: replay each step from a CUDA graph (qtt_step_graph); 0: launch the kernels")
     ap.add_argument("--workload", default="qtt1024_marmousi",
                     choices=["qtt1024_marmousi", "qtt512_64shots", "paper256", "variants", "fused", "qtt3d",
-                             "learned"],
+                             "learned", "gemm"],
                     help="qtt512_64shots: the batched multi-shot step; paper256: the paper's Sec. 5 run on the "
                          "synthetic stand-in; variants: boundary conditions and site orders")
     ap.add_argument("--fused-cfg", type=int, default=1, help="fused: the configuration index (1: 256x256 layered)")
@@ -1082,10 +1130,10 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned"):
+    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned", "gemm"):
         if rank == 0:
             fn = {"qtt512_64shots": run_shots, "paper256": run_paper, "variants": run_variants,
-                  "fused": run_fused, "qtt3d": run_3d, "learned": run_learned}[args.workload]
+                  "fused": run_fused, "qtt3d": run_3d, "learned": run_learned, "gemm": run_gemm}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:

@@ -102,7 +102,7 @@ def _check_forms(q, wl, c, amps, cases, prec, label):
         if prec == "fp64":
             assert got_r == want_r, (k, got_r, want_r)
         else:
-            assert ranks_ok(got_r, want_r, st, wl.eps), (k, got_r, want_r)
+            assert ranks_ok(got_r, want_r, st, wl.eps, wl.chi), (k, got_r, want_r)
         if degenerate:
             print(f"{label} {prec} step {k}: degenerate at FP32 resolution, not held to the bound")
             ndeg += 1

@@ -329,3 +329,37 @@ def test_fused_and_two_zipup_steps_agree_to_the_truncation():
     a = O.mps_to_dense(O.mps_step(Lm, C, lam2, prev, cur, 1e-9, INF, (3, 4), 0.5, n, order), n, order)
     b = O.mps_to_dense(O.mps_step_fused(A, prev, cur, 1e-9, INF, (3, 4), 0.5, n, order), n, order)
     assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-7
+
+
+def test_fused_step_loses_stability_under_truncation():
+    """A measured property of the fused variant (Eq. 7 applied by one
+    truncated zip-up), pinned so that the finding stays reproducible: on the
+    64 x 64 workload with chi = 64 (the cap never binds) and eps = 1e-10, the
+    two-zip-up step stays within 1e-3 of the dense Eq. 2 run for 200 steps,
+    while the fused step's error grows by more than 10x between step 100 and
+    step 200: truncating A psi = 2 psi + lambda^2 C^2 L psi as a whole, before
+    psi^{k-1} is subtracted, injects errors the leapfrog recurrence amplifies."""
+    import workloads as W
+    wl = W.config(0)
+    n, N = wl.n, wl.N
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    amps = wl.source_amplitudes(c)
+    Lo = O.laplacian_mpo(n, wl.order, wl.bc)
+    Co = O.velocity_mps(c, n, wl.order, wl.eps_c, wl.chi_c)
+    A = O.a_operator_mpo(Lo, Co, lam2)
+    c2r = O.mps_to_dense(Co, n, wl.order)
+    src = (N // 2 + 1, N // 2)
+    a = [O.zero_mps(2 * n)] * 2
+    b = [O.zero_mps(2 * n)] * 2
+    up, uc = np.zeros((N, N)), np.zeros((N, N))
+    err = {}
+    for k in range(200):
+        a = [a[1], O.mps_step(Lo, Co, lam2, a[0], a[1], wl.eps, 64, src, float(amps[k]), n, wl.order)]
+        b = [b[1], O.mps_step_fused(A, b[0], b[1], wl.eps, 64, src, float(amps[k]), n, wl.order)]
+        up, uc = uc, O.fdtd_step(up, uc, c2r, lam2, wl.bc, src, float(amps[k]))
+        if k + 1 in (100, 200):
+            rel = lambda x: np.linalg.norm(O.mps_to_dense(x, n, wl.order) - uc) / np.linalg.norm(uc)
+            err[k + 1] = (rel(a[1]), rel(b[1]))
+    assert err[200][0] < 1e-3, err
+    assert err[200][1] > 10 * err[100][1] and err[200][1] > 0.1, err

@@ -299,11 +299,11 @@ def paper_run() -> Workload:
 def qtt3d_run(n: int = 6) -> Workload:
     """The 3D extension's workload: a 2^n-per-axis layered and folded block
     (20 interfaces, 1600 -> 4500 m/s under a water layer, seed 7), dh = 20 m,
-    Ricker 15 Hz at (N/2, N/2, 2), chi_max = 64, eps = 1e-6, interleaved
-    order, periodic boundaries, 600 steps; receivers every 8 points along x
-    at y = N/2, z = 2."""
+    Ricker 8 Hz (about 12 points per wavelength at 2000 m/s) at (N/2, N/2, 2),
+    chi_max = 64, eps = 1e-6, interleaved order, periodic boundaries, 600
+    steps; receivers every 8 points along x at y = N/2, z = 2."""
     N = 1 << n
-    return Workload(f"qtt{N}_3d_layered", n, 20.0, 15.0, 600, 64, 1e-6, "interleaved", "periodic", "fp64",
+    return Workload(f"qtt{N}_3d_layered", n, 20.0, 8.0, 600, 64, 1e-6, "interleaved", "periodic", "fp64",
                     "layered3d", 7, 64, 1e-8, [(N // 2, N // 2, 2)], [(8 * i, N // 2, 2) for i in range(N // 8)],
                     dims=3)
 
