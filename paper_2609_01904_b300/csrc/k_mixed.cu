@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(NT32) jacobi32_cluster_kernel(const double* __
 // B rounds of cross pairs after), and writes the blocks back.  One cluster
 // barrier per block round instead of one per pair round.
 template <int EA, int EJ, int B>
-__global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
+__global__ void __launch_bounds__(NT32, 1) jacobi32_block_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
                                                               Dim m_d, double* __restrict__ Jout, long long ldj,
                                                               int max_sweeps, float tol, float tol_abs, int* log) {
   constexpr int MST = 128 * EA, JST = 128 * EJ, W = 2 * B;
@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
   float* wA = hJ + 2 * B * JST;               // working copy of the current block pair
   float* wJ = wA + W * MST;
   __shared__ int s_cnt;
+  __shared__ float s_nrm[W];  // squared norms of the working columns, tracked through the rotations
   const int nv = (int)dv(nv_d), m = (int)dv(m_d);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -237,6 +238,23 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
         }
       }
       __syncthreads();
+      // squared norms of the 2B working columns (warp q: columns q and q + B);
+      // a rotation then updates them exactly (|x'|^2 = a - t g, |y'|^2 = b + t g),
+      // so a pair needs one dot product instead of three
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4* xc = reinterpret_cast<const float4*>(wA + (warp + h * B) * MST);
+        float a = 0.f;
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+          const float4 v = xc[lane + 32 * e];
+          a = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, a))));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) s_nrm[warp + h * B] = a;
+      }
+      __syncthreads();
       // full local sweep over the 2B columns
       // block round 0 meets every block once: a full local sweep there covers
       // all pairs inside blocks; the other rounds rotate only the B x B pairs
@@ -276,19 +294,13 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
             u[e] = ui[lane + 32 * e];
             w[e] = uj[lane + 32 * e];
           }
-          float a = 0.f, b = 0.f, g = 0.f;
+          const float a = s_nrm[i], b = s_nrm[j];
+          float g = 0.f;
 #pragma unroll
-          for (int e = 0; e < EA; ++e) {
-            a = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, fmaf(x[e].z, x[e].z, fmaf(x[e].w, x[e].w, a))));
-            b = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, fmaf(y[e].z, y[e].z, fmaf(y[e].w, y[e].w, b))));
+          for (int e = 0; e < EA; ++e)
             g = fmaf(x[e].x, y[e].x, fmaf(x[e].y, y[e].y, fmaf(x[e].z, y[e].z, fmaf(x[e].w, y[e].w, g))));
-          }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-            g += __shfl_xor_sync(0xffffffffu, g, o);
-          }
+          for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
           if (g != 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b) && fabsf(g) > tol_abs * fmaxf(a, b)) {
             const float zeta = (b - a) / (2.f * g);
             const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -308,6 +320,10 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
                                               cs * p.w - sn * r.w);
               uj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
                                               sn * p.w + cs * r.w);
+            }
+            if (lane == 0) {
+              s_nrm[i] = fmaxf(a - tt * g, 0.f);
+              s_nrm[j] = fmaxf(b + tt * g, 0.f);
             }
             rot = 1;
           }
@@ -355,6 +371,323 @@ __global__ void __launch_bounds__(NT32) jacobi32_block_kernel(const double* __re
       if (c >= nv) continue;
       for (int l = tid; l < nv; l += NT32) Jout[(long long)c * ldj + l] = (double)hJ[(s2 * B + k) * JST + l];
     }
+}
+
+// Block one-sided Jacobi with the Gram matrix of each block pair (the block
+// method of Becka, Oksa & Vajtersic: a block pair is orthogonalised by the
+// eigenvectors of its 2B x 2B Gram matrix, applied to the pair as one small
+// product).  Same cluster, blocks and block rounds (circle method) as
+// jacobi32_block_kernel; in each block round a CTA
+//   1. pulls its two blocks (B columns each, rows of 2B floats in a working
+//      area, vectors and rotation columns) from the CTAs that held them in the
+//      previous block round, into the other of its two working areas,
+//   2. forms their Gram matrix G = X^T X (FP32, every entry a plain dot
+//      product, so its error is relative to |x_i| |x_j|),
+//   3. runs the rotations of the block round on G two-sidedly, one phase and
+//      one barrier per round of disjoint pairs: every entry of R^T G R comes
+//      from four entries of G (double-buffered), the rotations are
+//      accumulated in a 2B x 2B orthogonal V, and sixteen lanes compute the
+//      next round's rotations from the same four-entry formula meanwhile.  The
+//      rotation of a pair is the one one-sided Jacobi takes from the same
+//      columns, and the two-sided updates keep every entry's error relative to
+//      its own scale (Demmel & Veselic, the accuracy of Jacobi on positive
+//      definite matrices),
+//   4. if anything rotated, applies X <- X V and J <- J V as dense products
+//      (one warp per row, V's column in registers).
+// A rotation then costs a few shared-memory words of G instead of two vectors
+// of length m, and the vector work becomes two dense 2B-wide products per
+// block round, skipped where nothing rotates.
+namespace jg {
+
+// position (CTA, half) of block b in block round t of the circle method
+__device__ __forceinline__ void owner(int b, int t, int NB, int CS, int& r, int& h) {
+  if (b == NB - 1) {
+    r = 0;
+    h = 0;
+  } else if (b == t) {
+    r = 0;
+    h = 1;
+  } else {
+    int d = b - t;
+    if (d < 0) d += NB - 1;
+    if (d >= 1 && d <= CS - 1) {
+      r = d;
+      h = 0;
+    } else {
+      d = t - b;
+      if (d < 0) d += NB - 1;
+      r = d;
+      h = 1;
+    }
+  }
+}
+
+// the two blocks of CTA `rank` in block round t
+__device__ __forceinline__ void blocks(int t, int rank, int NB, int& bp, int& bq) {
+  if (rank == 0) {
+    bp = NB - 1;
+    bq = t;
+  } else {
+    bp = t + rank;
+    if (bp >= NB - 1) bp -= NB - 1;
+    bq = t - rank;
+    if (bq < 0) bq += NB - 1;
+  }
+}
+
+// pair q of local round lr: all pairs of the 2B columns in block round 0
+// (circle method over 2B), the B x B cross pairs (w, B + (w + lr) mod B) after
+template <int B>
+__device__ __forceinline__ void pair_of(int t, int lr, int q, int& i, int& j) {
+  constexpr int R = 2 * B - 1;
+  if (t != 0) {
+    i = q;
+    j = B + (q + lr) % B;
+  } else if (q == 0) {
+    i = R;
+    j = lr;
+  } else {
+    i = lr + q;
+    if (i >= R) i -= R;
+    j = lr - q;
+    if (j < 0) j += R;
+  }
+}
+
+// rotation parameters of index x: x' = cs x + sp partner, new diagonal, partner
+// and an active flag packed in w
+__device__ __forceinline__ float4 prm(float cs, float sp, float dn, int partner, bool act) {
+  return make_float4(cs, sp, dn, __int_as_float(partner | (act ? 256 : 0)));
+}
+
+}  // namespace jg
+
+template <int EA, int EJ, int B>
+__global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
+                                                             Dim m_d, double* __restrict__ Jout, long long ldj,
+                                                             int max_sweeps, float tol, float tol_abs, int* log) {
+  constexpr int MST = 128 * EA, JST = 128 * EJ, W = 2 * B, GS = W + 1, NSL = NT32 / 32 / 2;
+  // one working area: the two blocks' vectors ([MST][B] each) then their
+  // rotation columns ([JST][B] each), every block contiguous (so a pull from
+  // another CTA reads whole lines) and the second of each pair offset by 16
+  // floats (so a row of 2B columns spans all 32 banks)
+  constexpr int HA = MST * B + 16, HJ = JST * B + 16, AREA = 2 * HA + 2 * HJ;
+  static_assert(B == NT32 / 32 && W == 32, "32 working columns, one per lane; one pair per warp");
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks(), NB = 2 * CS;
+  extern __shared__ float4 sm4[];
+  float* area = reinterpret_cast<float*>(sm4);  // two working areas
+  float* gp = area + 2 * AREA;                  // partial Gram matrices: NSL x W x W
+  float* G = gp + NSL * W * W;                  // W x GS
+  float* Vr = G + W * GS;                       // W x GS
+  __shared__ float4 P[W];                       // rotation parameters of the current round, per index
+  __shared__ int s_cnt, s_any;
+  const int nv = (int)dv(nv_d), m = (int)dv(m_d);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // column c (0 .. 2B-1) of row r of the vectors / rotation columns of an area
+  auto xa = [&](float* ar, int r, int c) -> float& { return ar[(c >> 4) * HA + r * B + (c & 15)]; };
+  auto ja = [&](float* ar, int r, int c) -> float& { return ar[2 * HA + (c >> 4) * HJ + r * B + (c & 15)]; };
+
+  // block round 0 layout in area 0
+  {
+    int b0, b1;
+    jg::blocks(0, rank, NB, b0, b1);
+    for (int h = 0; h < 2; ++h)
+      for (int k = 0; k < B; ++k) {
+        const int c = (h ? b1 : b0) * B + k;
+        for (int l = tid; l < MST; l += NT32) xa(area, l, h * B + k) = (c < nv && l < m) ? (float)V[c * ldv + l] : 0.f;
+        for (int l = tid; l < JST; l += NT32) ja(area, l, h * B + k) = (c < nv && l == c) ? 1.f : 0.f;
+      }
+  }
+  int gr = 0, t_last = 0;  // block rounds done; block round of the data in the last area written
+  int sweep = 0;
+  for (sweep = 0; sweep < max_sweeps && nv >= 2; ++sweep) {
+    if (tid == 0) s_cnt = 0;
+    int rot = 0;  // this CTA rotated a pair in this sweep (uniform across the CTA)
+    cl.sync();
+    for (int t = 0; t < NB - 1; ++t, ++gr) {
+      int bp, bq;
+      jg::blocks(t, rank, NB, bp, bq);
+      float* cur = area + (gr & 1) * AREA;
+      // 1. pull the two blocks from their positions of the previous block round
+      //    (the first block round starts from the load above)
+      if (gr > 0) {
+        const int tp = t == 0 ? NB - 2 : t - 1;
+        static_assert(B * MST / 4 == NT32 * EA && B * JST / 4 == NT32 * EJ, "one float4 per thread and unit");
+        float4 ra[2][EA], rj[2][EJ];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int orank, oh;
+          jg::owner(h ? bq : bp, tp, NB, CS, orank, oh);
+          const float* src = cl.map_shared_rank(area + ((gr - 1) & 1) * AREA, orank);
+          const float4* sA = reinterpret_cast<const float4*>(src + oh * HA);
+          const float4* sJ = reinterpret_cast<const float4*>(src + 2 * HA + oh * HJ);
+#pragma unroll
+          for (int u = 0; u < EA; ++u) ra[h][u] = sA[tid + u * NT32];
+#pragma unroll
+          for (int u = 0; u < EJ; ++u) rj[h][u] = sJ[tid + u * NT32];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float4* dA = reinterpret_cast<float4*>(cur + h * HA);
+          float4* dJ = reinterpret_cast<float4*>(cur + 2 * HA + h * HJ);
+#pragma unroll
+          for (int u = 0; u < EA; ++u) dA[tid + u * NT32] = ra[h][u];
+#pragma unroll
+          for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
+        }
+      }
+      t_last = t;
+      if (tid == 0) s_any = 0;
+      __syncthreads();
+      // 2. Gram matrix: warp (half, slice) sums rows slice, slice + NSL, ... for
+      //    G rows half*16 .. half*16+15 against column `lane`
+      {
+        const int half = warp & 1, sl = warp >> 1;
+        float acc[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) acc[p] = 0.f;
+        const float* xl = cur + (lane >> 4) * HA + (lane & 15);
+        const float* xh = cur + half * HA;
+#pragma unroll 4
+        for (int r = sl; r < m; r += NSL) {
+          const float xq = xl[r * B];
+          const float4* xr = reinterpret_cast<const float4*>(xh + r * B);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 v = xr[u];
+            acc[4 * u + 0] = fmaf(v.x, xq, acc[4 * u + 0]);
+            acc[4 * u + 1] = fmaf(v.y, xq, acc[4 * u + 1]);
+            acc[4 * u + 2] = fmaf(v.z, xq, acc[4 * u + 2]);
+            acc[4 * u + 3] = fmaf(v.w, xq, acc[4 * u + 3]);
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < 16; ++p) gp[(sl * W + half * 16 + p) * W + lane] = acc[p];
+      }
+      __syncthreads();
+      for (int e = tid; e < W * W; e += NT32) {
+        float g = 0.f;
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) g += gp[sl * W * W + e];
+        G[(e / W) * GS + e % W] = g;
+        Vr[(e / W) * GS + e % W] = (e / W == e % W) ? 1.f : 0.f;
+      }
+      __syncthreads();
+      // 3. the block round's rotations on G, accumulated in V.  Each round:
+      //    (a) lanes 0..15 of warp 0 compute the rotations of the round's 16
+      //    pairs (one lane per pair, so the transcendental unit sees each
+      //    rotation once) and publish them per index; barrier; (b) warp w
+      //    writes rows i, j of its pair w of R^T G R (four entries of G each,
+      //    the partners' rotations from (a)) and columns i, j of V R; barrier
+      const int nlr = t == 0 ? W - 1 : B;
+      for (int lr = 0; lr < nlr; ++lr) {
+        if (tid < B) {
+          int i, j;
+          jg::pair_of<B>(t, lr, tid, i, j);
+          const float a = G[i * GS + i], b = G[j * GS + j], g = G[i * GS + j];
+          const int gi = (i < B ? bp : bq) * B + (i % B), gj = (j < B ? bp : bq) * B + (j % B);
+          const bool go = gi < nv && gj < nv && g != 0.f && fabsf(g) * rsqrtf(a) * rsqrtf(b) > tol &&
+                          fabsf(g) > tol_abs * fmaxf(a, b);
+          if (go) {
+            const float zeta = __fdividef(b - a, 2.f * g);
+            const float tt = copysignf(__fdividef(1.f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
+            const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
+            P[i] = jg::prm(cs, -sn, fmaxf(fmaf(-tt, g, a), 0.f), j, true);
+            P[j] = jg::prm(cs, sn, fmaxf(fmaf(tt, g, b), 0.f), i, true);
+            s_any = 1;
+          } else {
+            P[i] = jg::prm(1.f, 0.f, a, j, false);
+            P[j] = jg::prm(1.f, 0.f, b, i, false);
+          }
+        }
+        __syncthreads();
+        int i, j;
+        jg::pair_of<B>(t, lr, warp, i, j);
+        const float4 pi = P[i];
+        const bool go = (__float_as_int(pi.w) & 256) != 0;
+        const float cs = pi.x, sn = -pi.y;
+        {
+          const float4 pl = P[lane];
+          const int ql = __float_as_int(pl.w) & 255;
+          const float gil = G[i * GS + lane], gjl = G[j * GS + lane];
+          const float giq = G[i * GS + ql], gjq = G[j * GS + ql];
+          __syncwarp();
+          // rows first (this pair), then columns (the pair of `lane`)
+          const float ril = fmaf(-sn, gjl, cs * gil), riq = fmaf(-sn, gjq, cs * giq);
+          const float rjl = fmaf(sn, gil, cs * gjl), rjq = fmaf(sn, giq, cs * gjq);
+          float ni = fmaf(pl.y, riq, pl.x * ril), nj = fmaf(pl.y, rjq, pl.x * rjl);
+          if (go) {  // the pair's own 2 x 2 block in closed form
+            if (lane == i) {
+              ni = pi.z;
+              nj = 0.f;
+            } else if (lane == j) {
+              ni = 0.f;
+              nj = P[j].z;
+            }
+          }
+          G[i * GS + lane] = ni;
+          G[j * GS + lane] = nj;
+          if (go) {
+            const float vi = Vr[lane * GS + i], vj = Vr[lane * GS + j];
+            Vr[lane * GS + i] = fmaf(-sn, vj, cs * vi);
+            Vr[lane * GS + j] = fmaf(sn, vi, cs * vj);
+          }
+        }
+        __syncthreads();
+      }
+      // 4. X <- X V, J <- J V when something rotated
+      if (s_any) {
+        rot = 1;
+        float vq[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) vq[k] = Vr[k * GS + lane];
+        auto apply = [&](float* X0, int hs, int rows) {
+          float* X1 = X0 + hs;
+#pragma unroll 2
+          for (int r = warp; r < rows; r += NT32 / 32) {
+            const float4* x0 = reinterpret_cast<const float4*>(X0 + r * B);
+            const float4* x1 = reinterpret_cast<const float4*>(X1 + r * B);
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll
+            for (int u = 0; u < W / 4; ++u) {
+              const float4 v = u < B / 4 ? x0[u] : x1[u - B / 4];
+              o0 = fmaf(v.x, vq[4 * u], o0);
+              o1 = fmaf(v.y, vq[4 * u + 1], o1);
+              o2 = fmaf(v.z, vq[4 * u + 2], o2);
+              o3 = fmaf(v.w, vq[4 * u + 3], o3);
+            }
+            __syncwarp();
+            (lane < B ? X0 : X1)[r * B + (lane & 15)] = (o0 + o1) + (o2 + o3);
+          }
+        };
+        apply(cur, HA, m);
+        apply(cur + 2 * HA, HJ, nv < JST ? nv : JST);
+      }
+      if (t == NB - 2 && rot && tid == 0) s_cnt = 1;  // a flag, not a count: only zero matters
+      cl.sync();
+    }
+    int total = 0;
+    for (int r = 0; r < CS; ++r) total += *cl.map_shared_rank(&s_cnt, r);
+    cl.sync();  // every CTA has read the flags before the next sweep resets them
+    if (total == 0) break;
+  }
+  if (log && rank == 0 && tid == 0) {
+    log[0] = nv;
+    log[1] = m;
+    log[2] = sweep + 1;
+  }
+  {
+    int b0, b1;
+    jg::blocks(t_last, rank, NB, b0, b1);
+    float* fin = area + (gr > 0 ? (gr - 1) & 1 : 0) * AREA;
+    for (int h = 0; h < 2; ++h)
+      for (int k = 0; k < B; ++k) {
+        const int c = (h ? b1 : b0) * B + k;
+        if (c >= nv) continue;
+        for (int l = tid; l < nv; l += NT32) Jout[(long long)c * ldj + l] = (double)ja(fin, l, h * B + k);
+      }
+  }
 }
 
 // H = 1.5 I - 0.5 G  (the Newton-Schulz factor)
@@ -863,6 +1196,13 @@ static cudaError_t launch_j32(cudaLaunchConfig_t* cfg, const double* V, long lon
                             log);
 }
 
+// dynamic shared memory of jacobi32_gram_kernel: two working areas, partial
+// Gram matrices, G and V
+static size_t jg_smem(int EA, int EJ) {
+  constexpr int B = NT32 / 32, W = 2 * B, NSL = NT32 / 32 / 2;
+  return ((size_t)2 * (W * 128 * (EA + EJ) + 64) + (size_t)NSL * W * W + 2 * (size_t)W * (W + 1)) * sizeof(float);
+}
+
 template <int EA, int EJ>
 static size_t j32_smem(int cpc, int CS) {
   return (size_t)cpc * 128 * (EA + EJ) * sizeof(float) + 2 * (size_t)cpc * CS * sizeof(void*);
@@ -898,7 +1238,7 @@ cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim n
     constexpr int Bk = NT32 / 32;
     int CSb = 1;
     while (CSb < 16 && 2LL * CSb * Bk < nvmax) CSb *= 2;
-    const size_t sm_b = (size_t)4 * Bk * 128 * (EA + EJ) * sizeof(float);
+    const size_t sm_b = jg_smem(EA, EJ);
     if (2LL * CSb * Bk >= nvmax && sm_b <= (size_t)budget && (EA == EJ) && EA <= 2) {
       cfg.gridDim = dim3(CSb);
       at[0].val.clusterDim.x = CSb;
@@ -906,9 +1246,9 @@ cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim n
       const int max_sweeps = 20;
       const float tol = 1e-4f, tol_abs = 1e-6f;
       if (EA == 1)
-        return cudaLaunchKernelEx(&cfg, jacobi32_block_kernel<1, 1, Bk>, V, ldv, nv, m, J, ldj, max_sweeps, tol,
+        return cudaLaunchKernelEx(&cfg, jacobi32_gram_kernel<1, 1, Bk>, V, ldv, nv, m, J, ldj, max_sweeps, tol,
                                   tol_abs, log);
-      return cudaLaunchKernelEx(&cfg, jacobi32_block_kernel<2, 2, Bk>, V, ldv, nv, m, J, ldj, max_sweeps, tol, tol_abs,
+      return cudaLaunchKernelEx(&cfg, jacobi32_gram_kernel<2, 2, Bk>, V, ldv, nv, m, J, ldj, max_sweeps, tol, tol_abs,
                                 log);
     }
   }
@@ -1013,10 +1353,15 @@ static cudaError_t init_j32() {
 
 template <int EA, int EJ>
 static cudaError_t init_jb() {
-  const void* k = (const void*)jacobi32_block_kernel<EA, EJ, NT32 / 32>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const void* ks[2] = {(const void*)jacobi32_block_kernel<EA, EJ, NT32 / 32>,
+                       (const void*)jacobi32_gram_kernel<EA, EJ, NT32 / 32>};
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 static cudaError_t init_qrcp() {

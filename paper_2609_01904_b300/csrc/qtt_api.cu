@@ -169,7 +169,7 @@ void ws_free(qtt_ctx* ctx) {
   Workspace& s = ctx->ws;
   double** bufs[] = {&s.d_carry, &s.d_x, &s.d_tv, &s.d_tq, &s.d_rv, &s.d_jv, &s.d_jp, &s.d_w1,
                      &s.d_tt, &s.d_qt, &s.d_jh, &s.d_rg, &s.d_rh, &s.d_rt, &s.d_rw, &s.d_tau,
-                     &s.d_sig, &s.d_norm, &s.d_disc, &s.d_scale};
+                     &s.d_sig, &s.d_norm, &s.d_disc, &s.d_scale, &s.d_gpart};
   for (double** b : bufs)
     if (*b) {
       cudaFree(*b);
@@ -289,6 +289,8 @@ qtt_status ws_alloc(qtt_ctx* ctx, const Sizes& z, const Caps& c) {
   CK(cudaMalloc(&s.d_norm, s.vec * sizeof(double)));
   CK(cudaMalloc(&s.d_disc, 3 * (d + 1) * sizeof(double)));
   CK(cudaMalloc(&s.d_scale, 2 * sizeof(double)));
+  s.gnv = std::min<long long>(z.nvmax, 256);
+  CK(cudaMalloc(&s.d_gpart, (size_t)kGramChunks * s.gnv * s.gnv * sizeof(double)));
   CK(cudaMalloc(&s.d_ints, 4 * (d + 8) * sizeof(int)));
   CK(cudaMalloc(&s.d_flags, (s.vec + 64) * sizeof(int)));
   CK(cudaMalloc(&s.d_sync, sizeof(DevSync)));
@@ -568,9 +570,14 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     return fail(QTT_EINVAL, "internal: SVD larger than the workspace");
   double* sig = sigma_out ? sigma_out : s.d_sig;
   int* kq = s.d_ints + 0;
-  // The Gram matrix costs nv^2 ell FP64 FMAs, the QR about 4 us per column
-  // (its chain of reflectors): up to nv ell = 2^20 the Gram route is cheaper.
-  if (ellmax > nvmax && ctx->use_mp && nvmax <= 256 && ldv * nvmax <= s.tv && nvmax * ellmax <= (1LL << 20)) {
+  // The Gram matrix costs nv^2 ell / 2 FP64 FMAs spread over all SMs (split
+  // over the vector length), the QR about 4 us per column (its chain of
+  // reflectors) plus the pivoted QR of R0^T: up to nv ell = 2^25 (every bond
+  // of the 1024x1024 and 2048x2048 workloads' mixed SVDs) the Gram route is
+  // the cheaper, and on the tall zip-up bonds of diag(c^2) it is also the more
+  // accurate of the two (the QR route rounds M itself in FP32).
+  if (ellmax > nvmax && ctx->use_mp && nvmax <= 256 && nvmax <= s.gnv && ldv * nvmax <= s.tv &&
+      nvmax * ellmax <= (1LL << 25)) {
     // Preconditioned Jacobi (Drmac & Veselic 2008) on the rows of the
     // triangular factor of a QR with column pivoting of M, formed without
     // touching M again: G = M^T M in FP64, G = R^T R by Cholesky with
@@ -580,20 +587,8 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     // singular vectors of M are the rows of W / |W_c|, re-orthonormalised in
     // FP64.
     int* kr = s.d_ints + 1;
-    GemmArgs g = gemm0();  // G[a][c] = sum_l Tv[a][l] Tv[c][l]
-    g.A = Tv;
-    g.B = Tv;
-    g.C = s.d_tt;
-    g.M = nv;
-    g.N = nv;
-    g.K = ell;
-    g.sai = ell;
-    g.sak = dconst(1);
-    g.sbk = dconst(1);
-    g.sbj = ell;
-    g.sci = dconst(ldv);
-    g.scj = dconst(1);
-    KL(KC_PIVOT, gemm_d(ctx, g, nvmax, nvmax, 1, 1, ctx->stream));
+    // G[a][c] = sum_l Tv[a][l] Tv[c][l]
+    KL2(KC_PIVOT, gram_f64(Tv, ell, nv, ell, nvmax, ellmax, s.d_tt, ldv, s.d_gpart, kGramChunks, ctx->stream));
     KL(KC_PIVOT, pchol_cluster(ctx, s.d_tt, ldv, nv, ell, nvmax, s.d_rv, ldv, kr));
     CKS(jacobi_any(ctx, s.d_rv, ldv, dptr(kr), nv, nvmax, nvmax, s.d_jv, ldv, s.d_norm));
     // jacobi_any leaves W = J R in the refinement buffer

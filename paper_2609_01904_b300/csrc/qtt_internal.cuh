@@ -207,6 +207,8 @@ struct Workspace {
   double* d_norm = nullptr;   // vector norms from the Jacobi sweeps
   double* d_disc = nullptr;   // discarded weights per (phase, bond)
   double* d_scale = nullptr;  // power-of-two state scaling of a reduced-precision step (2^s, 2^-s)
+  double* d_gpart = nullptr;  // partial Gram products (kGramChunks x gnv^2) of the mixed SVD
+  long long gnv = 0;          // vectors the partial buffer holds
   int* d_ints = nullptr;      // scratch ints (ranks of temporaries)
   DevSync* d_sync = nullptr;
   // learned form: spectra of the last round (row k = bond k, ws_nvmax wide),
@@ -344,6 +346,13 @@ cudaError_t gemm_f64(const GemmArgs& a, long long Mmax, long long Nmax, long lon
 // the same product with FP32 arithmetic (the reduced-precision form)
 cudaError_t gemm_f32(const GemmArgs& a, long long Mmax, long long Nmax, long long nb1max,
                      long long nb2max, cudaStream_t st, int tile = 0);
+// G (ld ldg) = X X^T for nv vectors X_i at X + i*ldx of length ell, FP64,
+// split over the length into at most max_chunks partial products in P
+// (max_chunks * nvmax * nvmax doubles), upper tiles only, reduced in a fixed
+// order
+cudaError_t gram_f64(const double* X, Dim ldx, Dim nv, Dim ell, long long nvmax, long long ellmax, double* G,
+                     long long ldg, double* P, int max_chunks, cudaStream_t st);
+constexpr int kGramChunks = 16;
 // the same product on the tensor cores (tcgen05, accumulator in TMEM): kind
 // 0 = TF32, 1 = 3xTF32 (hi/lo split, ~FP32 accuracy), 2 = BF16; FP32
 // accumulation; bn = 64, 128 or 256 columns per CTA (128 rows); waits
