@@ -195,7 +195,7 @@ def roofline(prof: dict, prof_steps: int, ms_per_step: float, form: str, peaks: 
     pipe = pipes.get(dom)
     peak = peaks.get(f"{pipe}_tflops") if pipe else None
     achieved = fl.get(dom, 0.0) / (ms[dom] / 1e3) / 1e12 if ms[dom] > 0 else None
-    kernel = {"jacobi": "jacobi32_block_kernel (one-sided Jacobi SVD, FP32, one cluster)" if form != "fp64"
+    kernel = {"jacobi": "jacobi32_gram_kernel (block one-sided Jacobi SVD, FP32, one cluster)" if form != "fp64"
               else "jacobi_kernel (one-sided Jacobi SVD, FP64, cooperative)"}.get(dom, dom)
     roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if (achieved and peak) else None,
@@ -216,10 +216,11 @@ def roofline(prof: dict, prof_steps: int, ms_per_step: float, form: str, peaks: 
         # DRAM bytes of one 256-vector launch of the FP32 block Jacobi, from an
         # ncu capture of this kernel on the same workload (the input matrix,
         # read once); per launch, like `achieved`
-        roof["traffic"] = 592.9e3
-        roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of one jacobi32_block_kernel launch "
-                                "(ncu --set full -k regex:jacobi32_block -c 3 on python bench.py --steps 1 --warmup 3 "
-                                "--compare 0 --no-cpu-baseline)")
+        roof["traffic"] = 591.6e3
+        roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of one jacobi32_gram_kernel<2,2,16> "
+                                "launch (ncu --set full --clock-control none -k regex:jacobi32_gram_kernel -s 30 -c 1 "
+                                "on python bench.py --steps 1 --warmup 3 --compare 0 --no-cpu-baseline "
+                                "--e2e-steps 0); `achieved` averages all Jacobi launches of the step")
     return roof
 
 
@@ -483,6 +484,142 @@ def run_shots(args):
         "sequential": {"ms_per_batch_step": seq_ms, "value": ns / (seq_ms / 1e3),
                        "note": "the same 64 shot-steps issued one after another on one stream"},
         "speedup_vs_sequential": seq_ms / ms_per_step,
+        "clocks": clk.summary(),
+        "step_ms": [round(x, 3) for x in step_ms],
+    }
+
+
+def run_combined(args):
+    """The combined form on the 64-shot workload: FP32 form, batched shots,
+    learned ranks (the network of _train_rank_model, one range-finder sketch
+    shared by the shots).  The learned rounding reads each accept flag on the
+    host, so the batched steps are launched, not replayed from graphs.
+    Throughput: shot-steps/s over the timed batched steps.  Accuracy: for a
+    sample of shots (one per bond cap up to 128, the FP64 form at cap 256
+    costs seconds per step), the same steps from the same starting states in
+    the plain FP64 form and in the plain FP32 form; the fields after those
+    steps are compared (relative L2), and each form's per-shot step time is
+    reported."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+
+    mlp, training = _train_rank_model(q, "fp32")
+    wl = W.config(SHOTS_IDX)
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    chis = [int(x) for x in W.chi_per_shot(wl.seed, len(wl.sources))]
+    ns = len(chis)
+    nsteps = args.warmup + args.steps
+    amps = wl.source_amplitudes(c, SHOTS_MID_RUN + nsteps + 4)
+    stream = torch.cuda.Stream()
+    t0 = time.time()
+    batch = q.qtt_batch_create(wl.n, ns, chis, order=wl.order, bc=wl.bc, chi_max=max(chis), eps=wl.eps,
+                               chi_c=wl.chi_c, eps_c=wl.eps_c, prec="fp32", stream=stream, learned=True)
+    q.qtt_batch_set_graphs(batch, False)
+    N = wl.N
+    G = torch.as_tensor(W.gaussian_sketch(11, 1024, 512), device="cuda")
+    with torch.cuda.stream(stream):
+        c_dev = torch.as_tensor(c, device="cuda")
+        C = q.qtt_velocity_mps(batch.ctxs[0], c_dev)
+        L = q.qtt_laplacian_mpo(batch.ctxs[0])
+        c2 = c_dev * c_dev
+        prev, cur = [], []
+        for s in range(ns):
+            up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+            uc, un = up.clone(), up.clone()
+            for k in range(SHOTS_MID_RUN):
+                q.qtt_fdtd_step(batch.ctxs[s], c2, lam2, up, uc, un, wl.sources[s], float(amps[k]))
+                up, uc, un = uc, un, up
+            prev.append(q.qtt_mps_from_dense(batch.ctxs[s], up))
+            cur.append(q.qtt_mps_from_dense(batch.ctxs[s], uc))
+    stream.synchronize()
+    for x in batch.ctxs:
+        q.qtt_set_rank_model(x, mlp, G)
+    sample = []
+    for cap in (32, 64, 128):
+        hit = [s for s in range(ns) if chis[s] == cap]
+        if hit:
+            sample.append(hit[0])
+    start = {s: (q.qtt_mps_get_cores(prev[s]), q.qtt_mps_get_cores(cur[s])) for s in sample}
+    setup_s = time.time() - t0
+    k = SHOTS_MID_RUN
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            q.qtt_step_batched(batch, L, C, lam2, prev, cur, wl.sources, [float(amps[k])] * ns)
+            k += 1
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    for x in batch.ctxs:
+        q.qtt_profile_start(x, timing=False, log_svd=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                q.qtt_step_batched(batch, L, C, lam2, prev, cur, wl.sources, [float(amps[k])] * ns)
+                evs[i][1].record(stream)
+                k += 1
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    value = ns * args.steps / (float(np.sum(step_ms)) / 1e3)
+    profs = [q.qtt_profile_read(x) for x in batch.ctxs]
+    launches = sum(sum(p["launches"].values()) for p in profs)
+    att = acc = 0
+    for x in batch.ctxs:
+        a, b = q.qtt_learned_stats(x)
+        att += a
+        acc += b
+
+    def dense(psi):
+        out = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        q.qtt_to_dense(psi, out)
+        q.qtt_ctx_sync(psi.ctx)
+        return out.cpu().numpy()
+
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    shots = []
+    for s in sample:
+        got = dense(cur[s])
+        ref = {}
+        for form in ("fp64", "fp32"):
+            st = torch.cuda.Stream()
+            ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=chis[s], eps=wl.eps, chi_c=wl.chi_c,
+                                   eps_c=wl.eps_c, prec=form, stream=st)
+            with torch.cuda.stream(st):
+                Cf = q.qtt_velocity_mps(ctx, c_dev)
+                Lf = q.qtt_laplacian_mpo(ctx)
+                p0, c0 = q.qtt_mps_from_cores(ctx, start[s][0]), q.qtt_mps_from_cores(ctx, start[s][1])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for kk in range(nsteps):
+                    q.qtt_step(Lf, Cf, lam2, p0, c0, wl.sources[s], float(amps[SHOTS_MID_RUN + kk]))
+                e1.record(st)
+            st.synchronize()
+            ref[form] = (dense(c0), e0.elapsed_time(e1) / nsteps)
+            del Cf, Lf, p0, c0, ctx
+        shots.append({"shot": s, "chi": chis[s], "steps": nsteps,
+                      "field_rel_l2_combined_vs_fp64": rel(got, ref["fp64"][0]),
+                      "field_rel_l2_plain_fp32_vs_fp64": rel(ref["fp32"][0], ref["fp64"][0]),
+                      "ms_per_step_fp64": round(ref["fp64"][1], 2), "ms_per_step_plain_fp32": round(ref["fp32"][1], 2)})
+    for x in batch.ctxs:
+        q.qtt_set_rank_model(x, None, None)
+    return {
+        "metric": "MPS shot-steps/s, 64 shots on a 2^18 grid, combined form (FP32 + batched + learned ranks)",
+        "value": value, "unit": "shot-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic (seeded layered section; Ricker sources)",
+        "config": {"workload": wl.name + "_combined", "n": wl.n, "shots": ns, "chi_per_shot": chis, "eps": wl.eps,
+                   "graph": False, "state": f"mid-run (step {SHOTS_MID_RUN})",
+                   "l2": "flushed between timed steps (256 MiB write)", "setup_s": round(setup_s, 1)},
+        "training": training,
+        "range_finder_attempts": att, "range_finder_accepts": acc,
+        "svd_work_flop_per_step": sum(p["svd_flops"] for p in profs) / args.steps,
+        "gpu_launches": int(launches),
+        "accuracy_sample": shots,
+        "accuracy_note": "sample shots advanced warmup + steps steps from the same start in each form; "
+                         "errors of the fields at the end against the plain FP64 form",
         "clocks": clk.summary(),
         "step_ms": [round(x, 3) for x in step_ms],
     }
@@ -800,20 +937,14 @@ def run_3d(args):
             "forms": out}
 
 
-def run_learned(args):
-    """The learned rounding against plain rounding on the 2048x2048 section
-    (n = 11, chi = 256, eps = 1e-5).  Training data: the plain solver's round
-    spectra (qtt_step_features) and next-step ranks logged over teacher-free
-    steps from mid-run states of the 256x256 layered section, the 1024x1024
-    section and the 512x512 layered section at chi = 256; the network (40 ->
-    128 -> 128 -> 1) is trained on the GPU by the library (mean squared error,
-    Adam).  Then the same mid-run state of the 2048x2048 section is advanced
-    err_steps steps with plain rounding and with the learned rounding: the
-    logged Jacobi SVD work, the step times and the field difference between
-    the two (and against the dense Eq. 2 run) are reported."""
+def _train_rank_model(q, form):
+    """The learned rounding's network, trained on the GPU by the library on
+    the plain solver's round spectra (qtt_step_features) and next-step ranks,
+    logged over teacher-free steps from mid-run states of the 256x256 layered
+    section, the 1024x1024 section and the 512x512 layered section at
+    chi = 256 (40 -> 128 -> 128 -> 1, mean squared error, Adam).  Returns the
+    network and a description of its training."""
     import torch
-    from paper_2609_01904_b300 import qtt as q
-    form = args.form
     feats, labels, sources = [], [], []
     X = None
     for idx, nsteps, chi_o in ((1, 40, None), (2, 12, None), (3, 12, 256)):
@@ -851,6 +982,25 @@ def run_learned(args):
         q.qtt_mlp_grad(mlp, Xg, yg, loss)
         q.qtt_mlp_adam_step(mlp, 2e-3)
     loss1 = float(loss.item())
+    return mlp, {"samples": int(len(Xs)), "loss_start": loss0, "loss_end": loss1, "sources": sources}
+
+
+def run_learned(args):
+    """The learned rounding against plain rounding on the 2048x2048 section
+    (n = 11, chi = 256, eps = 1e-5).  Training data: the plain solver's round
+    spectra (qtt_step_features) and next-step ranks logged over teacher-free
+    steps from mid-run states of the 256x256 layered section, the 1024x1024
+    section and the 512x512 layered section at chi = 256; the network (40 ->
+    128 -> 128 -> 1) is trained on the GPU by the library (mean squared error,
+    Adam).  Then the same mid-run state of the 2048x2048 section is advanced
+    err_steps steps with plain rounding and with the learned rounding: the
+    logged Jacobi SVD work, the step times and the field difference between
+    the two (and against the dense Eq. 2 run) are reported."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    form = args.form
+    mlp, training = _train_rank_model(q, form)
+    loss0, loss1, sources = training["loss_start"], training["loss_end"], training["sources"]
     # evaluation on the 2048x2048 section
     wl = W.config(4)
     c = wl.velocity()
@@ -904,7 +1054,7 @@ def run_learned(args):
             "data": "synthetic (seeded Marmousi-shaped sections; Ricker sources)",
             "config": {"workload": wl.name, "n": wl.n, "chi_max": wl.chi, "eps": wl.eps,
                        "state": f"mid-run (step {mid} of {wl.steps})", "training": sources,
-                       "training_samples": int(len(Xs)), "loss_first_last": [loss0, loss1],
+                       "training_samples": training["samples"], "loss_first_last": [loss0, loss1],
                        "timing": "launched steps (the learned form reads each accept flag on the host)"},
             "plain": res["plain"], "learned": res["learned"],
             "field_rel_l2_learned_vs_plain": rel(fields["learned"], fields["plain"]),
@@ -1113,7 +1263,7 @@ def main():
     ap.add_argument("--graph", type=int, default=1, help="1: replay each step from a CUDA graph (qtt_step_graph); 0: launch the kernels")
     ap.add_argument("--workload", default="qtt1024_marmousi",
                     choices=["qtt1024_marmousi", "qtt512_64shots", "paper256", "variants", "fused", "qtt3d",
-                             "learned", "gemm"],
+                             "learned", "gemm", "combined"],
                     help="qtt512_64shots: the batched multi-shot step; paper256: the paper's Sec. 5 run on the "
                          "synthetic stand-in; variants: boundary conditions and site orders")
     ap.add_argument("--fused-cfg", type=int, default=1, help="fused: the configuration index (1: 256x256 layered)")
@@ -1130,10 +1280,11 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned", "gemm"):
+    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned", "gemm", "combined"):
         if rank == 0:
             fn = {"qtt512_64shots": run_shots, "paper256": run_paper, "variants": run_variants,
-                  "fused": run_fused, "qtt3d": run_3d, "learned": run_learned, "gemm": run_gemm}[args.workload]
+                  "fused": run_fused, "qtt3d": run_3d, "learned": run_learned, "gemm": run_gemm,
+                  "combined": run_combined}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:

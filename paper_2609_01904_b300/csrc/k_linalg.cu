@@ -80,11 +80,14 @@ __device__ __forceinline__ void qr_form(T* x, long long j, long long m, T* tau, 
 template <typename T, int B>
 __device__ __forceinline__ void qr_apply(const T* v, T tj, T* y, long long j, long long m, T* red) {
   const int tid = threadIdx.x;
+  // every thread reads y[j] before the barriers of block_sum: thread 0
+  // overwrites it below, and no thread may see the new value
+  const T yj = y[j];
   T s = T(0);
   for (long long i = j + 1 + tid; i < m; i += B) s = fma(__ldcg(v + i), y[i], s);
   s = block_sum(s, red);
-  const T w = tj * (y[j] + s);
-  if (tid == 0) y[j] -= w;
+  const T w = tj * (yj + s);
+  if (tid == 0) y[j] = yj - w;
   for (long long i = j + 1 + tid; i < m; i += B) y[i] = fma(-w, __ldcg(v + i), y[i]);
   __syncthreads();
 }
@@ -173,11 +176,12 @@ __global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, D
       const T ti = __ldcg(tau + i);
       if (ti == T(0)) continue;
       const T* v = W + i * ldw;
+      const T yi = ysh[i];  // read before block_sum's barriers (thread 0 overwrites it below)
       T s = T(0);
       for (long long l = i + 1 + tid; l < m; l += B) s = fma(__ldcg(v + l), ysh[l], s);
       s = block_sum(s, red);
-      const T w = ti * (ysh[i] + s);
-      if (tid == 0) ysh[i] -= w;
+      const T w = ti * (yi + s);
+      if (tid == 0) ysh[i] = yi - w;
       for (long long l = i + 1 + tid; l < m; l += B) ysh[l] = fma(-w, __ldcg(v + l), ysh[l]);
       __syncthreads();
     }

@@ -445,11 +445,11 @@ class Batch:
 
 def qtt_batch_create(n: int, nshots: int, chi_per_shot=None, order: str = "interleaved", bc: str = "periodic",
                      chi_max: int = 32, eps: float = 1e-10, chi_c: int = 0, eps_c: float = 0.0, prec: str = "fp64",
-                     stream=None) -> Batch:
+                     stream=None, learned: bool = False) -> Batch:
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, 0, 0.0, chi_c, eps_c, 0, 2)
+    p = qtt_params(n, ORDERS[order], BCS[bc], PRECISIONS[prec], chi_max, eps, 0, 0.0, chi_c, eps_c, int(learned), 2)
     chis = None
     if chi_per_shot is not None:
         chis = (ctypes.c_int * nshots)(*[int(x) for x in chi_per_shot])
@@ -460,7 +460,7 @@ def qtt_batch_create(n: int, nshots: int, chi_per_shot=None, order: str = "inter
     ctxs = []
     for i in range(nshots):
         chi_i = int(chi_per_shot[i]) if chi_per_shot is not None and int(chi_per_shot[i]) > 0 else chi_max
-        pi = qtt_params(p.n, p.order, p.bc, p.prec, chi_i, eps, 0, 0.0, chi_c, eps_c, 0, 2)
+        pi = qtt_params(p.n, p.order, p.bc, p.prec, chi_i, eps, 0, 0.0, chi_c, eps_c, int(learned), 2)
         ctxs.append(Ctx(_lib.qtt_batch_ctx(hold.h, i), pi, owner=hold))
     return Batch(hold, ctxs)
 
