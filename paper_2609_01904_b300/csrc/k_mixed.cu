@@ -467,11 +467,12 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
                                                              Dim m_d, double* __restrict__ Jout, long long ldj,
                                                              int max_sweeps, float tol, float tol_abs, int* log) {
   constexpr int MST = 128 * EA, JST = 128 * EJ, W = 2 * B, GS = W + 1, NSL = NT32 / 32 / 2;
-  // one working area: the two blocks' vectors ([MST][B] each) then their
-  // rotation columns ([JST][B] each), every block contiguous (so a pull from
-  // another CTA reads whole lines) and the second of each pair offset by 16
-  // floats (so a row of 2B columns spans all 32 banks)
-  constexpr int HA = MST * B + 16, HJ = JST * B + 16, AREA = 2 * HA + 2 * HJ;
+  // one working area: the two blocks' vectors ([MST][B] each), their
+  // rotation columns ([JST][B] each) and their B x B Gram matrices, every
+  // block contiguous (so a pull from another CTA reads whole lines) and the
+  // second of each pair offset by 16 floats (so a row of 2B columns spans all
+  // 32 banks)
+  constexpr int HA = MST * B + 16, HJ = JST * B + 16, HG = B * B, AREA = 2 * HA + 2 * HJ + 2 * HG;
   static_assert(B == NT32 / 32 && W == 32, "32 working columns, one per lane; one pair per warp");
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks(), NB = 2 * CS;
@@ -527,6 +528,15 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
 #pragma unroll
           for (int u = 0; u < EJ; ++u) rj[h][u] = sJ[tid + u * NT32];
         }
+        // the blocks' Gram matrices (rotated in the previous block round)
+        float4 rg = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int gh = tid / (HG / 4), gq = tid % (HG / 4);
+        if (t != 0 && tid < 2 * HG / 4) {
+          int orank, oh;
+          jg::owner(gh ? bq : bp, tp, NB, CS, orank, oh);
+          const float* src = cl.map_shared_rank(area + ((gr - 1) & 1) * AREA, orank);
+          rg = reinterpret_cast<const float4*>(src + 2 * HA + 2 * HJ + oh * HG)[gq];
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float4* dA = reinterpret_cast<float4*>(cur + h * HA);
@@ -536,13 +546,19 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
 #pragma unroll
           for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
         }
+        if (t != 0 && tid < 2 * HG / 4) reinterpret_cast<float4*>(cur + 2 * HA + 2 * HJ + gh * HG)[gq] = rg;
       }
       t_last = t;
       if (tid == 0) s_any = 0;
       __syncthreads();
-      // 2. Gram matrix: warp (half, slice) sums rows slice, slice + NSL, ... for
-      //    G rows half*16 .. half*16+15 against column `lane`
-      {
+      // 2. Gram matrix.  In the first block round of a sweep every entry is a
+      //    fresh dot product (warp (half, slice) sums rows slice, slice + NSL,
+      //    ... for G rows half*16 .. half*16+15 against column `lane`); after
+      //    it only the cross block X_0^T X_1 is new, and the two diagonal
+      //    blocks are the blocks' Gram matrices as the previous block round
+      //    left them (rotated two-sidedly, so their errors stay relative to
+      //    each entry's scale), refreshed again at the next sweep
+      if (t == 0) {
         const int half = warp & 1, sl = warp >> 1;
         float acc[16];
 #pragma unroll
@@ -564,15 +580,50 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
         }
 #pragma unroll
         for (int p = 0; p < 16; ++p) gp[(sl * W + half * 16 + p) * W + lane] = acc[p];
-      }
-      __syncthreads();
-      for (int e = tid; e < W * W; e += NT32) {
-        float g = 0.f;
+        __syncthreads();
+        for (int e = tid; e < W * W; e += NT32) {
+          float g = 0.f;
 #pragma unroll
-        for (int sl = 0; sl < NSL; ++sl) g += gp[sl * W * W + e];
-        G[(e / W) * GS + e % W] = g;
-        Vr[(e / W) * GS + e % W] = (e / W == e % W) ? 1.f : 0.f;
+          for (int sl2 = 0; sl2 < NSL; ++sl2) g += gp[sl2 * W * W + e];
+          G[(e / W) * GS + e % W] = g;
+        }
+      } else {
+        // cross block: 32 slices of rows (warp, lane half), lane & 15 the column
+        // of the second block, 16 accumulators over the first block's columns
+        const int sl = warp * 2 + (lane >> 4), bcol = lane & 15;
+        float acc[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) acc[p] = 0.f;
+#pragma unroll 2
+        for (int r = sl; r < m; r += 2 * (NT32 / 32)) {
+          const float xq = cur[HA + r * B + bcol];
+          const float4* xr = reinterpret_cast<const float4*>(cur + r * B);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 v = xr[u];
+            acc[4 * u + 0] = fmaf(v.x, xq, acc[4 * u + 0]);
+            acc[4 * u + 1] = fmaf(v.y, xq, acc[4 * u + 1]);
+            acc[4 * u + 2] = fmaf(v.z, xq, acc[4 * u + 2]);
+            acc[4 * u + 3] = fmaf(v.w, xq, acc[4 * u + 3]);
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < 16; ++p) gp[(sl * 16 + p) * 16 + bcol] = acc[p];
+        __syncthreads();
+        for (int e = tid; e < 3 * HG; e += NT32) {
+          if (e < HG) {
+            const int a = e / 16, bb = e % 16;
+            float g = 0.f;
+            for (int sl2 = 0; sl2 < 2 * (NT32 / 32); ++sl2) g += gp[(sl2 * 16 + a) * 16 + bb];
+            G[a * GS + B + bb] = g;
+            G[(B + bb) * GS + a] = g;
+          } else {
+            const int f = e - HG, h = f / HG, a = (f % HG) / B, bb = f % B;
+            G[(h * B + a) * GS + h * B + bb] = cur[2 * HA + 2 * HJ + h * HG + a * B + bb];
+          }
+        }
       }
+      for (int e = tid; e < W * W; e += NT32) Vr[(e / W) * GS + e % W] = (e / W == e % W) ? 1.f : 0.f;
       __syncthreads();
       // 3. the block round's rotations on G, accumulated in V.  Each round:
       //    (a) lanes 0..15 of warp 0 compute the rotations of the round's 16
@@ -635,6 +686,11 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
           }
         }
         __syncthreads();
+      }
+      // the blocks' rotated Gram matrices travel with them to the next block round
+      for (int e = tid; e < 2 * HG; e += NT32) {
+        const int h = e / HG, a = (e % HG) / B, bb = e % B;
+        cur[2 * HA + 2 * HJ + h * HG + a * B + bb] = G[(h * B + a) * GS + h * B + bb];
       }
       // 4. X <- X V, J <- J V when something rotated
       if (s_any) {
@@ -1196,11 +1252,12 @@ static cudaError_t launch_j32(cudaLaunchConfig_t* cfg, const double* V, long lon
                             log);
 }
 
-// dynamic shared memory of jacobi32_gram_kernel: two working areas, partial
-// Gram matrices, G and V
+// dynamic shared memory of jacobi32_gram_kernel: two working areas (with the
+// blocks' Gram matrices), partial Gram matrices, G and V
 static size_t jg_smem(int EA, int EJ) {
   constexpr int B = NT32 / 32, W = 2 * B, NSL = NT32 / 32 / 2;
-  return ((size_t)2 * (W * 128 * (EA + EJ) + 64) + (size_t)NSL * W * W + 2 * (size_t)W * (W + 1)) * sizeof(float);
+  return ((size_t)2 * (W * 128 * (EA + EJ) + 64 + 2 * B * B) + (size_t)NSL * W * W + 2 * (size_t)W * (W + 1)) *
+         sizeof(float);
 }
 
 template <int EA, int EJ>
