@@ -467,88 +467,152 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
                                                              Dim m_d, double* __restrict__ Jout, long long ldj,
                                                              int max_sweeps, float tol, float tol_abs, int* log) {
   constexpr int MST = 128 * EA, JST = 128 * EJ, W = 2 * B, GS = W + 1, NSL = NT32 / 32 / 2;
-  // one working area: the two blocks' vectors ([MST][B] each), their
-  // rotation columns ([JST][B] each) and their B x B Gram matrices, every
-  // block contiguous (so a pull from another CTA reads whole lines) and the
-  // second of each pair offset by 16 floats (so a row of 2B columns spans all
-  // 32 banks)
-  constexpr int HA = MST * B + 16, HJ = JST * B + 16, HG = B * B, AREA = 2 * HA + 2 * HJ + 2 * HG;
+  // working areas.  X role: the two blocks' vectors ([MST][B] each) and their
+  // B x B Gram matrices; J role: the two blocks' rotation columns ([JST][B]
+  // each).  Every block is contiguous (a pull from another CTA reads whole
+  // lines) and the second of a pair is offset by 16 floats (a row of 2B
+  // columns then spans all 32 banks)
+  constexpr int HA = MST * B + 16, HG = B * B, AREA = 2 * HA + 2 * HG;
+  constexpr int HJ = JST * B + 16, JAREA = 2 * HJ;
   static_assert(B == NT32 / 32 && W == 32, "32 working columns, one per lane; one pair per warp");
+  static_assert(B * MST / 4 == NT32 * EA && B * JST / 4 == NT32 * EJ, "one float4 per thread and unit");
   cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks(), NB = 2 * CS;
+  const int crank = (int)cl.block_rank(), CS = (int)cl.num_blocks() / 2, NB = 2 * CS;
+  const bool isJ = crank >= CS;                 // the second half of the cluster keeps the rotation columns
+  const int rank = isJ ? crank - CS : crank;    // the block pair this CTA follows
   extern __shared__ float4 sm4[];
-  float* area = reinterpret_cast<float*>(sm4);  // two working areas
-  float* gp = area + 2 * AREA;                  // partial Gram matrices: NSL x W x W
-  float* G = gp + NSL * W * W;                  // W x GS
-  float* Vr = G + W * GS;                       // W x GS
+  float* smf = reinterpret_cast<float*>(sm4);
+  float* area = smf;                            // X role: two working areas
+  float* gp = area + 2 * AREA;                  //   partial Gram matrices: NSL x W x W
+  float* G = gp + NSL * W * W;                  //   W x GS
+  float* Vr = G + W * GS;                       //   W x GS
+  float* jarea = smf;                           // J role: two working areas
+  float* vslot = jarea + 2 * JAREA;             //   the X partner's V of the last two block rounds (W x W)
   __shared__ float4 P[W];                       // rotation parameters of the current round, per index
-  __shared__ int s_cnt, s_any;
+  __shared__ int s_cnt, s_any, s_vflag[2];
   const int nv = (int)dv(nv_d), m = (int)dv(m_d);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // column c (0 .. 2B-1) of row r of the vectors / rotation columns of an area
-  auto xa = [&](float* ar, int r, int c) -> float& { return ar[(c >> 4) * HA + r * B + (c & 15)]; };
-  auto ja = [&](float* ar, int r, int c) -> float& { return ar[2 * HA + (c >> 4) * HJ + r * B + (c & 15)]; };
+  auto ja = [&](float* ar, int r, int c) -> float& { return ar[(c >> 4) * HJ + r * B + (c & 15)]; };
+  // rows [0, rows) of a pair of row-major [.][B] blocks (the second hs floats
+  // after the first) times the 2B x 2B rotation in vq (this lane's column)
+  auto apply = [&](float* X0, int hs, int rows, const float* vq) {
+    float* X1 = X0 + hs;
+#pragma unroll 2
+    for (int r = warp; r < rows; r += NT32 / 32) {
+      const float4* x0 = reinterpret_cast<const float4*>(X0 + r * B);
+      const float4* x1 = reinterpret_cast<const float4*>(X1 + r * B);
+      float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll
+      for (int u = 0; u < W / 4; ++u) {
+        const float4 v = u < B / 4 ? x0[u] : x1[u - B / 4];
+        o0 = fmaf(v.x, vq[4 * u], o0);
+        o1 = fmaf(v.y, vq[4 * u + 1], o1);
+        o2 = fmaf(v.z, vq[4 * u + 2], o2);
+        o3 = fmaf(v.w, vq[4 * u + 3], o3);
+      }
+      __syncwarp();
+      (lane < B ? X0 : X1)[r * B + (lane & 15)] = (o0 + o1) + (o2 + o3);
+    }
+  };
 
-  // block round 0 layout in area 0
+  // block round 0 layout: vectors in X area 0, the identity in J area 0
   {
     int b0, b1;
     jg::blocks(0, rank, NB, b0, b1);
     for (int h = 0; h < 2; ++h)
       for (int k = 0; k < B; ++k) {
         const int c = (h ? b1 : b0) * B + k;
-        for (int l = tid; l < MST; l += NT32) xa(area, l, h * B + k) = (c < nv && l < m) ? (float)V[c * ldv + l] : 0.f;
-        for (int l = tid; l < JST; l += NT32) ja(area, l, h * B + k) = (c < nv && l == c) ? 1.f : 0.f;
+        if (!isJ)
+          for (int l = tid; l < MST; l += NT32)
+            area[h * HA + l * B + k] = (c < nv && l < m) ? (float)V[c * ldv + l] : 0.f;
+        else
+          for (int l = tid; l < JST; l += NT32) ja(jarea, l, h * B + k) = (c < nv && l == c) ? 1.f : 0.f;
       }
+    if (tid == 0) s_vflag[0] = s_vflag[1] = 0;
   }
-  int gr = 0, t_last = 0;  // block rounds done; block round of the data in the last area written
+  // J role, step g: the rotation columns of block round g follow their
+  // blocks (pulled from the J CTAs that held them in round g - 1) and take
+  // the V that the X partner sent in round g.  Step g runs while the X CTAs
+  // work on round g + 1, so it is off their critical path.
+  auto jstep = [&](int g) {
+    const int tg = g % (NB - 1);
+    int bp, bq;
+    jg::blocks(tg, rank, NB, bp, bq);
+    float* cur = jarea + (g & 1) * JAREA;
+    if (g > 0) {
+      const int tp = tg == 0 ? NB - 2 : tg - 1;
+      float4 rj[2][EJ];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int orank, oh;
+        jg::owner(h ? bq : bp, tp, NB, CS, orank, oh);
+        const float4* sJ =
+            reinterpret_cast<const float4*>(cl.map_shared_rank(jarea + ((g - 1) & 1) * JAREA, orank + CS) + oh * HJ);
+#pragma unroll
+        for (int u = 0; u < EJ; ++u) rj[h][u] = sJ[tid + u * NT32];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float4* dJ = reinterpret_cast<float4*>(cur + h * HJ);
+#pragma unroll
+        for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
+      }
+      __syncthreads();
+    }
+    if (s_vflag[g & 1]) {
+      float vq[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) vq[k] = vslot[(g & 1) * W * W + k * W + lane];
+      apply(cur, HJ, nv < JST ? nv : JST, vq);
+    }
+  };
+
+  int gr = 0, t_last = 0;  // block rounds done; block round of the last data
   int sweep = 0;
   for (sweep = 0; sweep < max_sweeps && nv >= 2; ++sweep) {
     if (tid == 0) s_cnt = 0;
     int rot = 0;  // this CTA rotated a pair in this sweep (uniform across the CTA)
     cl.sync();
     for (int t = 0; t < NB - 1; ++t, ++gr) {
+      t_last = t;
+      if (isJ) {
+        if (gr > 0) jstep(gr - 1);
+        cl.sync();
+        continue;
+      }
       int bp, bq;
       jg::blocks(t, rank, NB, bp, bq);
       float* cur = area + (gr & 1) * AREA;
-      // 1. pull the two blocks from their positions of the previous block round
-      //    (the first block round starts from the load above)
+      // 1. pull the two blocks (and after a sweep's first block round their
+      //    Gram matrices) from their positions of the previous block round
       if (gr > 0) {
         const int tp = t == 0 ? NB - 2 : t - 1;
-        static_assert(B * MST / 4 == NT32 * EA && B * JST / 4 == NT32 * EJ, "one float4 per thread and unit");
-        float4 ra[2][EA], rj[2][EJ];
+        float4 ra[2][EA];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           int orank, oh;
           jg::owner(h ? bq : bp, tp, NB, CS, orank, oh);
           const float* src = cl.map_shared_rank(area + ((gr - 1) & 1) * AREA, orank);
           const float4* sA = reinterpret_cast<const float4*>(src + oh * HA);
-          const float4* sJ = reinterpret_cast<const float4*>(src + 2 * HA + oh * HJ);
 #pragma unroll
           for (int u = 0; u < EA; ++u) ra[h][u] = sA[tid + u * NT32];
-#pragma unroll
-          for (int u = 0; u < EJ; ++u) rj[h][u] = sJ[tid + u * NT32];
         }
-        // the blocks' Gram matrices (rotated in the previous block round)
         float4 rg = make_float4(0.f, 0.f, 0.f, 0.f);
         const int gh = tid / (HG / 4), gq = tid % (HG / 4);
         if (t != 0 && tid < 2 * HG / 4) {
           int orank, oh;
           jg::owner(gh ? bq : bp, tp, NB, CS, orank, oh);
           const float* src = cl.map_shared_rank(area + ((gr - 1) & 1) * AREA, orank);
-          rg = reinterpret_cast<const float4*>(src + 2 * HA + 2 * HJ + oh * HG)[gq];
+          rg = reinterpret_cast<const float4*>(src + 2 * HA + oh * HG)[gq];
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float4* dA = reinterpret_cast<float4*>(cur + h * HA);
-          float4* dJ = reinterpret_cast<float4*>(cur + 2 * HA + h * HJ);
 #pragma unroll
           for (int u = 0; u < EA; ++u) dA[tid + u * NT32] = ra[h][u];
-#pragma unroll
-          for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
         }
-        if (t != 0 && tid < 2 * HG / 4) reinterpret_cast<float4*>(cur + 2 * HA + 2 * HJ + gh * HG)[gq] = rg;
+        if (t != 0 && tid < 2 * HG / 4) reinterpret_cast<float4*>(cur + 2 * HA + gh * HG)[gq] = rg;
       }
-      t_last = t;
       if (tid == 0) s_any = 0;
       __syncthreads();
       // 2. Gram matrix.  In the first block round of a sweep every entry is a
@@ -619,7 +683,7 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
             G[(B + bb) * GS + a] = g;
           } else {
             const int f = e - HG, h = f / HG, a = (f % HG) / B, bb = f % B;
-            G[(h * B + a) * GS + h * B + bb] = cur[2 * HA + 2 * HJ + h * HG + a * B + bb];
+            G[(h * B + a) * GS + h * B + bb] = cur[2 * HA + h * HG + a * B + bb];
           }
         }
       }
@@ -690,36 +754,19 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
       // the blocks' rotated Gram matrices travel with them to the next block round
       for (int e = tid; e < 2 * HG; e += NT32) {
         const int h = e / HG, a = (e % HG) / B, bb = e % B;
-        cur[2 * HA + 2 * HJ + h * HG + a * B + bb] = G[(h * B + a) * GS + h * B + bb];
+        cur[2 * HA + h * HG + a * B + bb] = G[(h * B + a) * GS + h * B + bb];
       }
-      // 4. X <- X V, J <- J V when something rotated
+      // 4. X <- X V when something rotated, and V to the J partner
       if (s_any) {
         rot = 1;
         float vq[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) vq[k] = Vr[k * GS + lane];
-        auto apply = [&](float* X0, int hs, int rows) {
-          float* X1 = X0 + hs;
-#pragma unroll 2
-          for (int r = warp; r < rows; r += NT32 / 32) {
-            const float4* x0 = reinterpret_cast<const float4*>(X0 + r * B);
-            const float4* x1 = reinterpret_cast<const float4*>(X1 + r * B);
-            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
-#pragma unroll
-            for (int u = 0; u < W / 4; ++u) {
-              const float4 v = u < B / 4 ? x0[u] : x1[u - B / 4];
-              o0 = fmaf(v.x, vq[4 * u], o0);
-              o1 = fmaf(v.y, vq[4 * u + 1], o1);
-              o2 = fmaf(v.z, vq[4 * u + 2], o2);
-              o3 = fmaf(v.w, vq[4 * u + 3], o3);
-            }
-            __syncwarp();
-            (lane < B ? X0 : X1)[r * B + (lane & 15)] = (o0 + o1) + (o2 + o3);
-          }
-        };
-        apply(cur, HA, m);
-        apply(cur + 2 * HA, HJ, nv < JST ? nv : JST);
+        apply(cur, HA, m, vq);
+        float* vs = cl.map_shared_rank(vslot + (gr & 1) * W * W, crank + CS);
+        for (int e = tid; e < W * W; e += NT32) vs[e] = Vr[(e / W) * GS + e % W];
       }
+      if (tid == 0) *cl.map_shared_rank(&s_vflag[gr & 1], crank + CS) = s_any;
       if (t == NB - 2 && rot && tid == 0) s_cnt = 1;  // a flag, not a count: only zero matters
       cl.sync();
     }
@@ -728,15 +775,19 @@ __global__ void __launch_bounds__(NT32, 1) jacobi32_gram_kernel(const double* __
     cl.sync();  // every CTA has read the flags before the next sweep resets them
     if (total == 0) break;
   }
-  if (log && rank == 0 && tid == 0) {
+  // the rotation columns of the last block round, then no CTA leaves while
+  // another may still read its shared memory
+  if (isJ && gr > 0) jstep(gr - 1);
+  cl.sync();
+  if (log && crank == 0 && tid == 0) {
     log[0] = nv;
     log[1] = m;
     log[2] = sweep + 1;
   }
-  {
+  if (isJ) {
     int b0, b1;
     jg::blocks(t_last, rank, NB, b0, b1);
-    float* fin = area + (gr > 0 ? (gr - 1) & 1 : 0) * AREA;
+    float* fin = jarea + (gr > 0 ? (gr - 1) & 1 : 0) * JAREA;
     for (int h = 0; h < 2; ++h)
       for (int k = 0; k < B; ++k) {
         const int c = (h ? b1 : b0) * B + k;
@@ -1252,12 +1303,14 @@ static cudaError_t launch_j32(cudaLaunchConfig_t* cfg, const double* V, long lon
                             log);
 }
 
-// dynamic shared memory of jacobi32_gram_kernel: two working areas (with the
-// blocks' Gram matrices), partial Gram matrices, G and V
+// dynamic shared memory of jacobi32_gram_kernel: the larger of the X role
+// (two working areas with the blocks' Gram matrices, partial Gram matrices,
+// G and V) and the J role (two working areas, two V slots)
 static size_t jg_smem(int EA, int EJ) {
   constexpr int B = NT32 / 32, W = 2 * B, NSL = NT32 / 32 / 2;
-  return ((size_t)2 * (W * 128 * (EA + EJ) + 64 + 2 * B * B) + (size_t)NSL * W * W + 2 * (size_t)W * (W + 1)) *
-         sizeof(float);
+  const size_t xr = (size_t)2 * (2 * (128 * EA * B + 16) + 2 * B * B) + (size_t)NSL * W * W + 2 * (size_t)W * (W + 1);
+  const size_t jr = (size_t)2 * (2 * (128 * EJ * B + 16)) + 2 * (size_t)W * W;
+  return std::max(xr, jr) * sizeof(float);
 }
 
 template <int EA, int EJ>
@@ -1296,9 +1349,10 @@ cudaError_t jacobi32_cluster(qtt_ctx* ctx, const double* V, long long ldv, Dim n
     int CSb = 1;
     while (CSb < 16 && 2LL * CSb * Bk < nvmax) CSb *= 2;
     const size_t sm_b = jg_smem(EA, EJ);
-    if (2LL * CSb * Bk >= nvmax && sm_b <= (size_t)budget && (EA == EJ) && EA <= 2) {
-      cfg.gridDim = dim3(CSb);
-      at[0].val.clusterDim.x = CSb;
+    if (2LL * CSb * Bk >= nvmax && CSb <= 8 && sm_b <= (size_t)budget && (EA == EJ) && EA <= 2) {
+      // CSb CTAs rotate the vectors, CSb more keep the rotation columns
+      cfg.gridDim = dim3(2 * CSb);
+      at[0].val.clusterDim.x = 2 * CSb;
       cfg.dynamicSmemBytes = sm_b;
       const int max_sweeps = 20;
       const float tol = 1e-4f, tol_abs = 1e-6f;
