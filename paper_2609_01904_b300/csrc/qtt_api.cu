@@ -502,8 +502,8 @@ GemmArgs gram(const double* X, long long ldx, double* G, long long ldg, Dim rows
 
 // One-sided Jacobi of nv vectors V (length m) in the step's precision.  The
 // mixed form: FP32 Jacobi in one cluster, then FP64 refinement (Newton-Schulz
-// and two damped first-order corrections from the Gram of W = J V, two
-// final Newton-Schulz steps), sigma = |W_c|.
+// and two damped first-order corrections from the Gram of W = J V, one
+// final Newton-Schulz step), sigma = |W_c|.
 qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, long long mmax,
                       double* J, long long ldj, double* norms) {
   if (!ctx->use_mp) {
@@ -531,7 +531,9 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
     KL(KC_REFINE, copy2d(s.d_rt, J, nv, nv, dconst(ld), dconst(1), dconst(ldj), dconst(1), nvmax * nvmax, 1.0,
                          ctx->stream));
   }
-  CKS(ns());
+  // after the second correction J is orthogonal to ~|Omega|^2 (FP64
+  // rounding once the FP32 stage reached its 1e-4 stop): one Newton-Schulz
+  // step takes it to rounding
   CKS(ns());
   KL(KC_REFINE, gemm_d(ctx, mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
   KL(KC_REFINE, row_norms(s.d_rw, ld, nv, m, nvmax, norms, ctx->stream));
@@ -593,7 +595,6 @@ qtt_status svd_vm(qtt_ctx* ctx, const double* Tv, Dim nv, Dim ell, long long nvm
     CKS(jacobi_any(ctx, s.d_rv, ldv, dptr(kr), nv, nvmax, nvmax, s.d_jv, ldv, s.d_norm));
     // jacobi_any leaves W = J R in the refinement buffer
     KL(KC_REFINE, scale_rows(s.d_rw, ldv, s.d_norm, dptr(kr), nv, nvmax, nvmax, s.d_jh, ldv, ctx->stream));
-    CKS(ns_rows(ctx, s.d_jh, ldv, dptr(kr), nv, nvmax, nvmax));
     CKS(ns_rows(ctx, s.d_jh, ldv, dptr(kr), nv, nvmax, nvmax));
     KL(KC_POST, svd_post(ctx, s.d_norm, dptr(kr), nv, nv, s.d_jh, ldv, eps, chi, rank_cap, rank_out, sig, disc_out,
                          Jp, Jt, nsv_out));
