@@ -17,7 +17,34 @@ namespace qtt {
 namespace {
 
 constexpr int NT = 256;
+constexpr int kQrQCols = 4;  // columns of the thin Q a CTA forms together
 constexpr int kRegE = 2;  // register-resident Jacobi pairs up to NT * kRegE = 512 elements
+
+// Block-wide sums of N values per thread (red: 32 N entries).
+template <typename T, int N>
+__device__ __forceinline__ void block_sum_n(T (&v)[N], T* red) {
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) red[32 * k + w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      T t = l < nw ? red[32 * k + l] : T(0);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (l == 0) red[32 * k] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = red[32 * k];
+  __syncthreads();
+}
 
 __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red /* 96 */) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -76,7 +103,10 @@ __device__ __forceinline__ void qr_form(T* x, long long j, long long m, T* tau, 
 }
 
 // y <- (I - tau v v^T) y on rows j..m-1 (v_j = 1 implicit); v is another CTA's
-// column, read through L2
+// column, read through L2 once: up to kApplyRegs entries per thread stay in
+// registers between the dot product and the update (the update is on the
+// reflector chain's critical path), longer columns are read twice
+constexpr int kApplyRegs = 4;
 template <typename T, int B>
 __device__ __forceinline__ void qr_apply(const T* v, T tj, T* y, long long j, long long m, T* red) {
   const int tid = threadIdx.x;
@@ -84,11 +114,33 @@ __device__ __forceinline__ void qr_apply(const T* v, T tj, T* y, long long j, lo
   // overwrites it below, and no thread may see the new value
   const T yj = y[j];
   T s = T(0);
-  for (long long i = j + 1 + tid; i < m; i += B) s = fma(__ldcg(v + i), y[i], s);
-  s = block_sum(s, red);
-  const T w = tj * (yj + s);
-  if (tid == 0) y[j] = yj - w;
-  for (long long i = j + 1 + tid; i < m; i += B) y[i] = fma(-w, __ldcg(v + i), y[i]);
+  if (m - (j + 1) <= (long long)kApplyRegs * B) {
+    T vr[kApplyRegs];
+#pragma unroll
+    for (int u = 0; u < kApplyRegs; ++u) {
+      const long long i = j + 1 + tid + (long long)u * B;
+      vr[u] = i < m ? __ldcg(v + i) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kApplyRegs; ++u) {
+      const long long i = j + 1 + tid + (long long)u * B;
+      if (i < m) s = fma(vr[u], y[i], s);
+    }
+    s = block_sum(s, red);
+    const T w = tj * (yj + s);
+    if (tid == 0) y[j] = yj - w;
+#pragma unroll
+    for (int u = 0; u < kApplyRegs; ++u) {
+      const long long i = j + 1 + tid + (long long)u * B;
+      if (i < m) y[i] = fma(-w, vr[u], y[i]);
+    }
+  } else {
+    for (long long i = j + 1 + tid; i < m; i += B) s = fma(__ldcg(v + i), y[i], s);
+    s = block_sum(s, red);
+    const T w = tj * (yj + s);
+    if (tid == 0) y[j] = yj - w;
+    for (long long i = j + 1 + tid; i < m; i += B) y[i] = fma(-w, __ldcg(v + i), y[i]);
+  }
   __syncthreads();
 }
 
@@ -96,8 +148,8 @@ template <typename T, int B>
 __global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, Dim lda_d, T* W, long long ldw,
                                                 Dim m_d, Dim n_d, T* tau, double* Rout, int r_rowmajor,
                                                 long long ldr, double* Qout, int* kq_out, int* flag,
-                                                DevSync* sync, double* flops) {
-  __shared__ T red[32];
+                                                DevSync* sync, double* flops, int qcols) {
+  __shared__ T red[32 * kQrQCols];
   __shared__ int s_ok;
   extern __shared__ unsigned char ysh_raw[];
   T* ysh = reinterpret_cast<T*>(ysh_raw);
@@ -165,27 +217,88 @@ __global__ void __launch_bounds__(B) qr_kernel(const double* __restrict__ Ain, D
   }
   if (!Qout || kq == 0) return;
 
-  // thin Q (m x kq, row-major): column c = H_0 ... H_c e_c, built in shared memory
+  // thin Q (m x kq, row-major): column c = H_0 ... H_c e_c, built in shared
+  // memory, kQrQCols columns of a CTA at a time: H_i is read once for all of
+  // them (its entries kept in registers between the dot products and the
+  // updates), so a CTA's time is its largest column's chain, not the sum
   if (tid == 0) s_ok = wait_geq(flag + kq - 1, 1, sync) ? 1 : 0;
   __syncthreads();
   if (!s_ok) return;
-  for (long long c = b; c < kq; c += G) {
-    for (long long i = tid; i < m; i += B) ysh[i] = (i == c) ? T(1) : T(0);
+  constexpr int QC = kQrQCols;
+  for (long long c0 = b; c0 < kq; c0 += (long long)G * qcols) {
+    long long cols[QC];
+    int nc = 0;
+#pragma unroll
+    for (int u = 0; u < QC; ++u) {
+      cols[u] = c0 + (long long)u * G;
+      if (u < qcols && cols[u] < kq) nc = u + 1;
+    }
+    for (int u = 0; u < nc; ++u)
+      for (long long i = tid; i < m; i += B) ysh[u * m + i] = (i == cols[u]) ? T(1) : T(0);
     __syncthreads();
-    for (long long i = c; i >= 0; --i) {
+    for (long long i = cols[nc - 1]; i >= 0; --i) {
       const T ti = __ldcg(tau + i);
       if (ti == T(0)) continue;
       const T* v = W + i * ldw;
-      const T yi = ysh[i];  // read before block_sum's barriers (thread 0 overwrites it below)
-      T s = T(0);
-      for (long long l = i + 1 + tid; l < m; l += B) s = fma(__ldcg(v + l), ysh[l], s);
-      s = block_sum(s, red);
-      const T w = ti * (yi + s);
-      if (tid == 0) ysh[i] = yi - w;
-      for (long long l = i + 1 + tid; l < m; l += B) ysh[l] = fma(-w, __ldcg(v + l), ysh[l]);
+      T yi[QC], dot[QC];
+#pragma unroll
+      for (int u = 0; u < QC; ++u) {  // read before the reduction's barriers (thread 0 overwrites them)
+        yi[u] = (u < nc && cols[u] >= i) ? ysh[u * m + i] : T(0);
+        dot[u] = T(0);
+      }
+      const bool regs = m - (i + 1) <= (long long)kApplyRegs * B;
+      T vr[kApplyRegs];
+      if (regs) {
+#pragma unroll
+        for (int e = 0; e < kApplyRegs; ++e) {
+          const long long l = i + 1 + tid + (long long)e * B;
+          vr[e] = l < m ? __ldcg(v + l) : T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < kApplyRegs; ++e) {
+          const long long l = i + 1 + tid + (long long)e * B;
+          if (l < m)
+#pragma unroll
+            for (int u = 0; u < QC; ++u)
+              if (u < nc && cols[u] >= i) dot[u] = fma(vr[e], ysh[u * m + l], dot[u]);
+        }
+      } else {
+        for (long long l = i + 1 + tid; l < m; l += B) {
+          const T vl = __ldcg(v + l);
+#pragma unroll
+          for (int u = 0; u < QC; ++u)
+            if (u < nc && cols[u] >= i) dot[u] = fma(vl, ysh[u * m + l], dot[u]);
+        }
+      }
+      block_sum_n<T, QC>(dot, red);
+      T w[QC];
+#pragma unroll
+      for (int u = 0; u < QC; ++u) w[u] = ti * (yi[u] + dot[u]);
+      if (tid == 0)
+#pragma unroll
+        for (int u = 0; u < QC; ++u)
+          if (u < nc && cols[u] >= i) ysh[u * m + i] = yi[u] - w[u];
+      if (regs) {
+#pragma unroll
+        for (int e = 0; e < kApplyRegs; ++e) {
+          const long long l = i + 1 + tid + (long long)e * B;
+          if (l < m)
+#pragma unroll
+            for (int u = 0; u < QC; ++u)
+              if (u < nc && cols[u] >= i) ysh[u * m + l] = fma(-w[u], vr[e], ysh[u * m + l]);
+        }
+      } else {
+        for (long long l = i + 1 + tid; l < m; l += B) {
+          const T vl = __ldcg(v + l);
+#pragma unroll
+          for (int u = 0; u < QC; ++u)
+            if (u < nc && cols[u] >= i) ysh[u * m + l] = fma(-w[u], vl, ysh[u * m + l]);
+        }
+      }
       __syncthreads();
     }
-    for (long long i = tid; i < m; i += B) Qout[i * kq + c] = (double)ysh[i];
+    for (int u = 0; u < nc; ++u)
+      for (long long i = tid; i < m; i += B) Qout[i * kq + cols[u]] = (double)ysh[u * m + i];
     __syncthreads();
   }
 }
@@ -432,7 +545,11 @@ static cudaError_t qr_launch(qtt_ctx* ctx, const double* Ain, Dim lda, double* W
                              long long qm_max, int block) {
   int grid = (int)std::min<long long>(ctx->coop_blocks, std::max<long long>(nmax, 1));
   size_t smem = 0;
-  if (Qout) smem = (size_t)qm_max * sizeof(T);
+  int qcols = 1;  // columns of Q formed together: as many as fit in shared memory, at most kQrQCols
+  if (Qout) {
+    while (qcols < kQrQCols && (size_t)(qcols + 1) * qm_max * sizeof(T) <= 200 * 1024) ++qcols;
+    smem = (size_t)qcols * qm_max * sizeof(T);
+  }
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   T* W = reinterpret_cast<T*>(Wd);
   T* tau = reinterpret_cast<T*>(ctx->ws.d_tau);
@@ -442,7 +559,7 @@ static cudaError_t qr_launch(qtt_ctx* ctx, const double* Ain, Dim lda, double* W
   double* flops = g_flop_ctr;
   void* args[] = {(void*)&Ain, (void*)&lda, (void*)&W, (void*)&ldw, (void*)&m, (void*)&n, (void*)&tau,
                   (void*)&Rout, (void*)&rrm, (void*)&ldr, (void*)&Qout, (void*)&kq_out, (void*)&flag,
-                  (void*)&sync, (void*)&flops};
+                  (void*)&sync, (void*)&flops, (void*)&qcols};
   // long columns (ldw bounds the rows): 1024 threads shorten each pass over a
   // column, which the reflector chain waits on
   if (block == 0) block = ldw >= 2048 ? 1024 : NT;
