@@ -501,9 +501,9 @@ GemmArgs gram(const double* X, long long ldx, double* G, long long ldg, Dim rows
 }
 
 // One-sided Jacobi of nv vectors V (length m) in the step's precision.  The
-// mixed form: FP32 Jacobi in one cluster, then FP64 refinement (Newton-Schulz
-// and two damped first-order corrections from the Gram of W = J V, one
-// final Newton-Schulz step), sigma = |W_c|.
+// mixed form: FP32 Jacobi in one cluster, then FP64 refinement (two damped
+// first-order corrections from the Gram of W = J V with a Newton-Schulz step
+// between them, one final Newton-Schulz step), sigma = |W_c|.
 qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, long long nvmax, long long mmax,
                       double* J, long long ldj, double* norms) {
   if (!ctx->use_mp) {
@@ -523,7 +523,10 @@ qtt_status jacobi_any(qtt_ctx* ctx, double* V, long long ldv, Dim nv, Dim m, lon
     return QTT_OK;
   };
   for (int it = 0; it < 2; ++it) {
-    CKS(ns());
+    // the FP32 rotation is orthogonal to ~1e-6: the first correction takes
+    // that in with the off-diagonal part, the Newton-Schulz step before the
+    // second one restores orthogonality to ~|Omega|^2
+    if (it > 0) CKS(ns());
     KL(KC_REFINE, gemm_d(ctx, mm(J, ldj, V, ldv, s.d_rw, ld, nv, nv, m), nvmax, mmax, 1, 1, ctx->stream));
     KL(KC_REFINE, gemm_d(ctx, gram(s.d_rw, ld, s.d_rg, ld, nv, m), nvmax, nvmax, 1, 1, ctx->stream));
     KL2(KC_REFINE, omega_factor(s.d_rg, norms, s.d_rh, ld, nv, nvmax, ctx->stream));  // two kernels; norms: scratch
