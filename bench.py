@@ -216,11 +216,12 @@ def roofline(prof: dict, prof_steps: int, ms_per_step: float, form: str, peaks: 
         # DRAM bytes of one 256-vector launch of the FP32 block Jacobi, from an
         # ncu capture of this kernel on the same workload (the input matrix,
         # read once); per launch, like `achieved`
-        roof["traffic"] = 591.6e3
+        roof["traffic"] = 597.0e3
         roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of one jacobi32_gram_kernel<2,2,16> "
-                                "launch (ncu --set full --clock-control none -k regex:jacobi32_gram_kernel -s 30 -c 1 "
-                                "on python bench.py --steps 1 --warmup 3 --compare 0 --no-cpu-baseline "
-                                "--e2e-steps 0); `achieved` averages all Jacobi launches of the step")
+                                "launch (16 CTAs: 8 rotating the vectors, 8 keeping the rotation columns; ncu --set "
+                                "full --clock-control none -k regex:jacobi32_gram_kernel -s 30 -c 1 on python "
+                                "bench.py --steps 1 --warmup 3 --compare 0 --no-cpu-baseline --e2e-steps 0); "
+                                "`achieved` averages all Jacobi launches of the step")
     return roof
 
 
