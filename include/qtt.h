@@ -377,9 +377,9 @@ qtt_status qtt_svd_trunc(qtt_ctx* ctx, const double* M_dev, int m, int n, double
  *   (NULL = legacy default stream); the call synchronises it.
  * Limits: max(m,n) <= 512 and min(m,n) <= 128, else QTT_EINVAL (message in
  * qtt_last_error).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the array: calls whose work overlaps on the GPU
- * (two streams, two threads) race and corrupt each other's results. */
+ * address (cudaGetSymbolAddress).  Every call shares the array: calls whose
+ * work overlaps on the GPU (two streams, two threads) race and corrupt each
+ * other's results. */
 qtt_status qtt_svd_trunc_noalloc(const double* M_dev, int m, int n, double eps, int chi, double* U_dev,
                                  double* S_dev, double* Vt_dev, int* rank_out, void* cuda_stream);
 
