@@ -865,6 +865,79 @@ def run_fused(args):
             "steps_compared": out}
 
 
+def run_full(args):
+    """The 1024x1024 workload run from its start: zero state, the Ricker
+    source, every step of the 4000-step run (or as many as fit in
+    --full-seconds of wall time) replayed from CUDA graphs in the chosen form;
+    steps/s over the whole run, the per-step time against the step index,
+    the ranks as they grow, and the field at the end against the dense Eq. 2
+    run of the same steps on the same GPU (the truncation error of the whole
+    run; the FP64 MPS is not a reference over thousands of steps, the
+    truncated dynamics being chaotic once the ranks reach chi)."""
+    import torch
+    from paper_2609_01904_b300 import qtt as q
+    wl = W.config(WORKLOAD_IDX)
+    c = wl.velocity()
+    lam2 = wl.lambda2(c)
+    N, total = wl.N, wl.steps
+    amps = wl.source_amplitudes(c, total + 2)
+    src = wl.sources[0]
+    stream = torch.cuda.Stream()
+    ctx = q.qtt_ctx_create(n=wl.n, order=wl.order, bc=wl.bc, chi_max=wl.chi, eps=wl.eps, chi_c=wl.chi_c,
+                           eps_c=wl.eps_c, prec=args.form, stream=stream)
+    with torch.cuda.stream(stream):
+        c_dev = torch.as_tensor(c, device="cuda")
+        C = q.qtt_velocity_mps(ctx, c_dev)
+        L = q.qtt_laplacian_mpo(ctx)
+        prev, cur = q.qtt_mps_create_zero(ctx), q.qtt_mps_create_zero(ctx)
+    step = q.qtt_step_graph if args.graph else q.qtt_step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(total)]
+    ranks_at, done = {}, 0
+    torch.cuda.synchronize()
+    t0 = time.time()
+    with ClockSampler(0) as clk:
+        for k in range(total):
+            with torch.cuda.stream(stream):
+                ev[k][0].record(stream)
+                step(L, C, lam2, prev, cur, src, float(amps[k]))
+                ev[k][1].record(stream)
+            done = k + 1
+            if done % 250 == 0 or done == total:
+                stream.synchronize()
+                ranks_at[done] = max(q.qtt_mps_ranks(cur))
+                if time.time() - t0 > args.full_seconds:
+                    break
+        torch.cuda.synchronize()
+    step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(done)]
+    # the dense run of the same steps, after the timed loop
+    c2 = c_dev * c_dev
+    up = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    uc, un = up.clone(), up.clone()
+    with torch.cuda.stream(stream):
+        for k in range(done):
+            q.qtt_fdtd_step(ctx, c2, lam2, up, uc, un, src, float(amps[k]))
+            up, uc, un = uc, un, up
+        mps = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        q.qtt_to_dense(cur, mps)
+    q.qtt_ctx_sync(ctx)
+    err = float(torch.linalg.norm(mps - uc) / max(float(torch.linalg.norm(uc)), 1e-300))
+    curve = {str(k + 1): round(step_ms[k], 3) for k in range(done) if k < 5 or (k + 1) % 100 == 0}
+    value = done / (float(np.sum(step_ms)) / 1e3)
+    return {"metric": "MPS steps/s over the whole run of the 1024x1024 workload (chi=128, eps=1e-6), 1 B300",
+            "value": value, "unit": "steps/s", "n_gpus": 1, "steps": done, "warmup": 0,
+            "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64"}.get(args.form, "f32+f64"), "form": args.form,
+            "data": "synthetic (seeded Marmousi-shaped velocity section; Ricker source)",
+            "config": {"workload": wl.name + "_full_run", "n": wl.n, "chi_max": wl.chi, "eps": wl.eps,
+                       "chi_c": wl.chi_c, "steps_planned": total, "graph": bool(args.graph),
+                       "timing": "sum of per-step CUDA-event times (host syncs every 250 steps fall between steps)"},
+            "per_step_ms": curve, "max_rank_at_step": ranks_at,
+            "ms_per_step_first_100": float(np.mean(step_ms[:100])),
+            "ms_per_step_last_100": float(np.mean(step_ms[-100:])),
+            "field_rel_l2_vs_dense_fdtd_at_end": err, "clocks": clk.summary(),
+            "wall_s": round(time.time() - t0, 1)}
+
+
 def run_3d(args):
     """The 3D extension (64^3 layered block, 3n = 18 sites, the 7-point
     Laplacian MPO, chi = 64, eps = 1e-6, Ricker source at (32, 32, 2)): MPS
@@ -1264,11 +1337,13 @@ def main():
     ap.add_argument("--graph", type=int, default=1, help="1: replay each step from a CUDA graph (qtt_step_graph); 0: launch the kernels")
     ap.add_argument("--workload", default="qtt1024_marmousi",
                     choices=["qtt1024_marmousi", "qtt512_64shots", "paper256", "variants", "fused", "qtt3d",
-                             "learned", "gemm", "combined"],
+                             "learned", "gemm", "combined", "full"],
                     help="qtt512_64shots: the batched multi-shot step; paper256: the paper's Sec. 5 run on the "
                          "synthetic stand-in; variants: boundary conditions and site orders")
     ap.add_argument("--fused-cfg", type=int, default=1, help="fused: the configuration index (1: 256x256 layered)")
     ap.add_argument("--fused-chi-zip", type=int, default=4, help="fused: the zip-up bond cap as a multiple of chi")
+    ap.add_argument("--full-seconds", type=float, default=420.0,
+                    help="full: stop the full run after this much wall time (the steps done are reported)")
     ap.add_argument("--png", default=None, help="paper256: write the FDTD | MPS field pair to this PNG file")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1281,11 +1356,12 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned", "gemm", "combined"):
+    if args.workload in ("qtt512_64shots", "paper256", "variants", "fused", "qtt3d", "learned", "gemm", "combined",
+                         "full"):
         if rank == 0:
             fn = {"qtt512_64shots": run_shots, "paper256": run_paper, "variants": run_variants,
                   "fused": run_fused, "qtt3d": run_3d, "learned": run_learned, "gemm": run_gemm,
-                  "combined": run_combined}[args.workload]
+                  "combined": run_combined, "full": run_full}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:
