@@ -159,225 +159,12 @@ __global__ void __launch_bounds__(NT32) jacobi32_cluster_kernel(const double* __
   }
 }
 
-// Block one-sided Jacobi.  The nv columns form 2*CS blocks of B columns;
-// block k lives in the shared memory of CTA k/2 (slot k%2).  A sweep is a
-// round-robin tournament over the blocks: in each of its 2*CS-1 block rounds
-// CTA r copies its pair of blocks into a local working area, rotates their
-// pairs (one warp per pair, rounds of B disjoint pairs separated by
-// __syncthreads only: all 2B-1 rounds of the 2B columns in block round 0, the
-// B rounds of cross pairs after), and writes the blocks back.  One cluster
-// barrier per block round instead of one per pair round.
-template <int EA, int EJ, int B>
-__global__ void __launch_bounds__(NT32, 1) jacobi32_block_kernel(const double* __restrict__ V, long long ldv, Dim nv_d,
-                                                              Dim m_d, double* __restrict__ Jout, long long ldj,
-                                                              int max_sweeps, float tol, float tol_abs, int* log) {
-  constexpr int MST = 128 * EA, JST = 128 * EJ, W = 2 * B;
-  static_assert(B == NT32 / 32, "one warp per pair of a local round");
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks(), NB = 2 * CS;
-  extern __shared__ float4 sm4[];
-  float* hA = reinterpret_cast<float*>(sm4);  // home: 2 blocks x B columns
-  float* hJ = hA + 2 * B * MST;
-  float* wA = hJ + 2 * B * JST;               // working copy of the current block pair
-  float* wJ = wA + W * MST;
-  __shared__ int s_cnt;
-  __shared__ float s_nrm[W];  // squared norms of the working columns, tracked through the rotations
-  const int nv = (int)dv(nv_d), m = (int)dv(m_d);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  for (int s2 = 0; s2 < 2; ++s2)
-    for (int k = 0; k < B; ++k) {
-      const int c = (2 * rank + s2) * B + k;
-      for (int l = tid; l < MST; l += NT32)
-        hA[(s2 * B + k) * MST + l] = (c < nv && l < m) ? (float)V[c * ldv + l] : 0.f;
-      for (int l = tid; l < JST; l += NT32) hJ[(s2 * B + k) * JST + l] = (c < nv && l == c) ? 1.f : 0.f;
-    }
-  int sweep = 0;
-  for (sweep = 0; sweep < max_sweeps && nv >= 2; ++sweep) {
-    if (tid == 0) s_cnt = 0;
-    int rot = 0;  // this thread's warp rotated a pair in this sweep
-    cl.sync();
-    for (int t = 0; t < NB - 1; ++t) {
-      // this CTA's block pair in block round t (circle method over NB blocks)
-      int bp, bq;
-      if (rank == 0) {
-        bp = NB - 1;
-        bq = t;
-      } else {
-        bp = t + rank;
-        if (bp >= NB - 1) bp -= NB - 1;
-        bq = t - rank;
-        if (bq < 0) bq += NB - 1;
-      }
-      const int blk[2] = {bp, bq};
-      // copy in (float4 through distributed shared memory): every thread
-      // issues all its remote loads before its first store, so the copy
-      // costs one round trip, not one per element
-      static_assert(B * MST / 4 == NT32 * EA && B * JST / 4 == NT32 * EJ, "one float4 per thread and unit");
-      {
-        float4 ra[2][EA], rj[2][EJ];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float4* srcA = reinterpret_cast<const float4*>(
-              cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
-          const float4* srcJ = reinterpret_cast<const float4*>(
-              cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
-#pragma unroll
-          for (int u = 0; u < EA; ++u) ra[h][u] = srcA[tid + u * NT32];
-#pragma unroll
-          for (int u = 0; u < EJ; ++u) rj[h][u] = srcJ[tid + u * NT32];
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float4* dA = reinterpret_cast<float4*>(wA + h * B * MST);
-          float4* dJ = reinterpret_cast<float4*>(wJ + h * B * JST);
-#pragma unroll
-          for (int u = 0; u < EA; ++u) dA[tid + u * NT32] = ra[h][u];
-#pragma unroll
-          for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
-        }
-      }
-      __syncthreads();
-      // squared norms of the 2B working columns (warp q: columns q and q + B);
-      // a rotation then updates them exactly (|x'|^2 = a - t g, |y'|^2 = b + t g),
-      // so a pair needs one dot product instead of three
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float4* xc = reinterpret_cast<const float4*>(wA + (warp + h * B) * MST);
-        float a = 0.f;
-#pragma unroll
-        for (int e = 0; e < EA; ++e) {
-          const float4 v = xc[lane + 32 * e];
-          a = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, a))));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) s_nrm[warp + h * B] = a;
-      }
-      __syncthreads();
-      // full local sweep over the 2B columns
-      // block round 0 meets every block once: a full local sweep there covers
-      // all pairs inside blocks; the other rounds rotate only the B x B pairs
-      // across their two blocks (round s pairs column w of the first block
-      // with column (w + s) mod B of the second), so each pair is visited
-      // once per sweep
-      const int nlr = t == 0 ? W - 1 : B;
-      for (int lr = 0; lr < nlr; ++lr) {
-        int i, j;
-        const int q = warp, R = W - 1;
-        if (t != 0) {
-          i = q;
-          j = B + (q + lr) % B;
-        } else if (q == 0) {
-          i = R;
-          j = lr;
-        } else {
-          i = lr + q;
-          if (i >= R) i -= R;
-          j = lr - q;
-          if (j < 0) j += R;
-        }
-        const int gi = blk[i / B] * B + (i % B), gj = blk[j / B] * B + (j % B);
-        if (gi < nv && gj < nv) {
-          float4* xi = reinterpret_cast<float4*>(wA + i * MST);
-          float4* xj = reinterpret_cast<float4*>(wA + j * MST);
-          float4* ui = reinterpret_cast<float4*>(wJ + i * JST);
-          float4* uj = reinterpret_cast<float4*>(wJ + j * JST);
-          float4 x[EA], y[EA], u[EJ], w[EJ];
-#pragma unroll
-          for (int e = 0; e < EA; ++e) {
-            x[e] = xi[lane + 32 * e];
-            y[e] = xj[lane + 32 * e];
-          }
-#pragma unroll
-          for (int e = 0; e < EJ; ++e) {
-            u[e] = ui[lane + 32 * e];
-            w[e] = uj[lane + 32 * e];
-          }
-          const float a = s_nrm[i], b = s_nrm[j];
-          float g = 0.f;
-#pragma unroll
-          for (int e = 0; e < EA; ++e)
-            g = fmaf(x[e].x, y[e].x, fmaf(x[e].y, y[e].y, fmaf(x[e].z, y[e].z, fmaf(x[e].w, y[e].w, g))));
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-          if (g != 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b) && fabsf(g) > tol_abs * fmaxf(a, b)) {
-            const float zeta = (b - a) / (2.f * g);
-            const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            const float cs = rsqrtf(1.f + tt * tt), sn = cs * tt;
-#pragma unroll
-            for (int e = 0; e < EA; ++e) {
-              const float4 p = x[e], r = y[e];
-              xi[lane + 32 * e] = make_float4(cs * p.x - sn * r.x, cs * p.y - sn * r.y, cs * p.z - sn * r.z,
-                                              cs * p.w - sn * r.w);
-              xj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
-                                              sn * p.w + cs * r.w);
-            }
-#pragma unroll
-            for (int e = 0; e < EJ; ++e) {
-              const float4 p = u[e], r = w[e];
-              ui[lane + 32 * e] = make_float4(cs * p.x - sn * r.x, cs * p.y - sn * r.y, cs * p.z - sn * r.z,
-                                              cs * p.w - sn * r.w);
-              uj[lane + 32 * e] = make_float4(sn * p.x + cs * r.x, sn * p.y + cs * r.y, sn * p.z + cs * r.z,
-                                              sn * p.w + cs * r.w);
-            }
-            if (lane == 0) {
-              s_nrm[i] = fmaxf(a - tt * g, 0.f);
-              s_nrm[j] = fmaxf(b + tt * g, 0.f);
-            }
-            rot = 1;
-          }
-        }
-        __syncthreads();
-      }
-      // copy back to the home CTAs (local loads first, then remote stores)
-      {
-        float4 ra[2][EA], rj[2][EJ];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float4* sA = reinterpret_cast<const float4*>(wA + h * B * MST);
-          const float4* sJ = reinterpret_cast<const float4*>(wJ + h * B * JST);
-#pragma unroll
-          for (int u = 0; u < EA; ++u) ra[h][u] = sA[tid + u * NT32];
-#pragma unroll
-          for (int u = 0; u < EJ; ++u) rj[h][u] = sJ[tid + u * NT32];
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float4* dA = reinterpret_cast<float4*>(cl.map_shared_rank(hA + (blk[h] & 1) * B * MST, blk[h] >> 1));
-          float4* dJ = reinterpret_cast<float4*>(cl.map_shared_rank(hJ + (blk[h] & 1) * B * JST, blk[h] >> 1));
-#pragma unroll
-          for (int u = 0; u < EA; ++u) dA[tid + u * NT32] = ra[h][u];
-#pragma unroll
-          for (int u = 0; u < EJ; ++u) dJ[tid + u * NT32] = rj[h][u];
-        }
-      }
-      if (t == NB - 2 && rot) s_cnt = 1;  // a flag, not a count: only zero matters
-      cl.sync();
-    }
-    int total = 0;
-    for (int r = 0; r < CS; ++r) total += *cl.map_shared_rank(&s_cnt, r);
-    cl.sync();  // every CTA has read the counters before the next sweep resets them
-    if (total == 0) break;
-  }
-  if (log && rank == 0 && tid == 0) {
-    log[0] = nv;
-    log[1] = m;
-    log[2] = sweep + 1;
-  }
-  for (int s2 = 0; s2 < 2; ++s2)
-    for (int k = 0; k < B; ++k) {
-      const int c = (2 * rank + s2) * B + k;
-      if (c >= nv) continue;
-      for (int l = tid; l < nv; l += NT32) Jout[(long long)c * ldj + l] = (double)hJ[(s2 * B + k) * JST + l];
-    }
-}
-
 // Block one-sided Jacobi with the Gram matrix of each block pair (the block
 // method of Becka, Oksa & Vajtersic: a block pair is orthogonalised by the
 // eigenvectors of its 2B x 2B Gram matrix, applied to the pair as one small
-// product).  Same cluster, blocks and block rounds (circle method) as
-// jacobi32_block_kernel; in each block round a CTA
+// product).  The nv columns form 2*CS blocks of B columns, and a sweep is a
+// round-robin tournament of the blocks (circle method, 2*CS - 1 block
+// rounds); in each block round a CTA
 //   1. pulls its two blocks (B columns each, rows of 2B floats in a working
 //      area, vectors and rotation columns) from the CTAs that held them in the
 //      previous block round, into the other of its two working areas,
@@ -1464,15 +1251,10 @@ static cudaError_t init_j32() {
 
 template <int EA, int EJ>
 static cudaError_t init_jb() {
-  const void* ks[2] = {(const void*)jacobi32_block_kernel<EA, EJ, NT32 / 32>,
-                       (const void*)jacobi32_gram_kernel<EA, EJ, NT32 / 32>};
-  for (const void* k : ks) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const void* k = (const void*)jacobi32_gram_kernel<EA, EJ, NT32 / 32>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 static cudaError_t init_qrcp() {
