@@ -340,7 +340,9 @@ qtt_status qtt_learned_stats(qtt_ctx* ctx, long* attempts, long* accepts);
 /* Receiver readout: out[p] = A_0[s_0] A_1[s_1] ... A_{d-1}[s_{d-1}] (Eq. 8)
  * at grid points (ix[p], iz[p]), p < count.  ix, iz, out: device arrays of
  * count int64 / int64 / double.  Indices are not range-checked on the
- * device; the caller keeps them in [0, N). */
+ * device; the caller keeps them in [0, N).  An index outside that range
+ * still reads only the state's cores: the kernel takes the 2n low bits of
+ * ix N + iz, so the value returned is that of another grid point. */
 qtt_status qtt_sample(qtt_ctx* ctx, const qtt_mps* psi, const long* ix_dev, const long* iz_dev,
                       long count, double* out_dev);
 
