@@ -186,7 +186,10 @@ qtt_status qtt_inject_source_3d(qtt_ctx* ctx, qtt_mps* psi, long ix, long iy, lo
  * src_ixiz: NULL for no source, else a host pair {ix, iz} ({ix, iy, iz} in
  * 3D) where src_amp is added to u^{k+1} as a rank-1 product state.  psi_cur must be right-
  * orthonormal in cores 1..d-1 (as every state this library returns is) for
- * the zip-up truncation to measure the right norm. */
+ * the zip-up truncation to measure the right norm.  Stability is the
+ * caller's: the leapfrog of Eq. 2 needs lambda2 * max(c^2) <= 1/2 (2D;
+ * 1/3 in 3D), which the paper does not state and the step does not check
+ * (the maximum of the c^2 MPS is not known without a dense evaluation). */
 qtt_status qtt_step(qtt_ctx* ctx, const qtt_mpo* L, const qtt_mps* c2, double lambda2,
                     qtt_mps* psi_prev, qtt_mps* psi_cur, const long* src_ixiz, double src_amp);
 
