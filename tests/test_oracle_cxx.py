@@ -17,6 +17,7 @@ on its own, against what the paper and the mathematics fix:
   1e-12, and its dense update equals a loop over grid points written here;
 * (c) a discrete eigenmode follows its closed-form cosine recurrence;
 * (d) separable fields have the closed-form QTT ranks;
+* the leapfrog energy of the untruncated step is conserved;
 * Eckart-Young on constructed spectra through the zip-up and the round.
 
 Then the two oracles are compared on truncated steps, where neither is a
@@ -356,6 +357,31 @@ def test_separable_fields_have_closed_form_ranks(order):
                     exp.append(rf(lev + 1) * rg(lev + 1))
                 exp[-1] = 1
             assert ranks == exp, (fa, ga, ranks, exp)
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_leapfrog_energy_is_conserved_by_the_untruncated_step(bc):
+    """Source-free, untruncated, variable c: the discrete energy of the Eq. 2
+    leapfrog, sum (u^{k+1} - u^k)^2 / c^2 - lambda^2 <u^{k+1}, L u^k>, is
+    constant to rounding for the symmetric 5-point L of either boundary."""
+    n, order = 3, "interleaved"
+    rng = np.random.default_rng(8)
+    c = rng.uniform(1.0, 2.0, (8, 8))
+    lam2 = 0.45 / (c * c).max()
+    C = X.velocity_mps(c, n, order, 0.0, INF)
+    c2 = X.mps_to_dense(C, n, order)
+    B = _stencil(n, bc)
+
+    def energy(u0, u1):
+        return float(np.sum((u1 - u0) ** 2 / c2) - lam2 * np.dot(u1.reshape(-1), B @ u0.reshape(-1)))
+
+    u_prev, u_cur = rng.standard_normal((8, 8)), rng.standard_normal((8, 8))
+    prev, cur = X.mps_from_dense(u_prev, n, order, 0.0, INF), X.mps_from_dense(u_cur, n, order, 0.0, INF)
+    E0 = energy(u_prev, u_cur)
+    for _ in range(40):
+        prev, cur = cur, X.mps_step(n, order, bc, C, lam2, prev, cur, 0.0, INF)
+    E = energy(X.mps_to_dense(prev, n, order), X.mps_to_dense(cur, n, order))
+    assert abs(E - E0) < 1e-11 * abs(E0)
 
 
 # ---------------------------------------------------------------------------
