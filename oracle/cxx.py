@@ -25,7 +25,6 @@ _LIB = os.path.join(_HERE, "libqtt_oracle_cxx.so")
 
 _ORDER = {"sequential": 0, "interleaved": 1}
 _BC = {"periodic": 0, "zero": 1}
-_AXIS = {"x": 0, "z": 1}
 
 _lib = None
 
@@ -53,25 +52,27 @@ def _load():
         "oc_mps_ranks": (None, [vp, ip]),
         "oc_mps_data": (None, [vp, dp]),
         "oc_mps_free": (None, [vp]),
-        "oc_mps_from_dense": (vp, [i, i, dp, d, i]),
-        "oc_mps_to_dense": (None, [vp, i, i, dp]),
-        "oc_mps_sample": (None, [vp, i, i, i, ip, ip, dp]),
-        "oc_product_state": (vp, [i, i, i, i]),
+        "oc_mps_from_dense": (vp, [i, i, i, dp, d, i]),
+        "oc_mps_to_dense": (None, [vp, i, i, i, dp]),
+        "oc_mps_sample": (None, [vp, i, i, i, i, ip, dp]),
+        "oc_product_state": (vp, [i, i, i, ip]),
         "oc_round": (vp, [vp, d, i]),
         "oc_sum": (vp, [i, dp, C.POINTER(vp)]),
-        "oc_shift_mpo": (vp, [i, i, i, i, i]),
-        "oc_laplacian_mpo": (vp, [i, i, i]),
-        "oc_laplacian_sum_of_shifts": (vp, [i, i, i]),
+        "oc_shift_mpo": (vp, [i, i, i, i, i, i]),
+        "oc_laplacian_mpo": (vp, [i, i, i, i]),
+        "oc_laplacian_sum_of_shifts": (vp, [i, i, i, i]),
         "oc_diagonal_mpo": (vp, [vp]),
+        "oc_a_operator_mpo": (vp, [vp, vp, d]),
         "oc_mpo_sites": (i, [vp]),
         "oc_mpo_bonds": (None, [vp, ip]),
         "oc_mpo_data": (None, [vp, dp]),
-        "oc_mpo_grid_operator": (None, [vp, i, i, dp]),
+        "oc_mpo_grid_operator": (None, [vp, i, i, i, dp]),
         "oc_mpo_free": (None, [vp]),
         "oc_zipup_lr": (vp, [vp, vp, d, i]),
         "oc_zipup_rl": (vp, [vp, vp, d, i]),
-        "oc_step": (vp, [vp, vp, d, vp, vp, d, i, i, i, d, i, i]),
-        "oc_fdtd_step": (None, [i, dp, dp, dp, d, i, i, i, d, dp]),
+        "oc_step": (vp, [vp, vp, d, vp, vp, d, i, ip, d, i, i, i]),
+        "oc_step_fused": (vp, [vp, vp, vp, d, i, ip, d, i, i, i]),
+        "oc_fdtd_step": (None, [i, i, dp, dp, dp, d, i, ip, d, dp]),
         "oc_svd": (i, [i, i, dp, dp, dp, dp]),
         "oc_qr": (None, [i, i, dp, dp, dp]),
         "oc_trunc_rank": (i, [i, dp, d, i]),
@@ -182,9 +183,18 @@ def trunc_rank(sigma, eps: float, chi: int) -> int:
     return int(_load().oc_trunc_rank(s.size, _dp(s), float(eps), int(chi)))
 
 
+def _dims(u) -> int:
+    return 3 if np.ndim(u) == 3 else 2
+
+
+def _pt(p) -> np.ndarray:
+    return np.ascontiguousarray(p, dtype=np.int32)
+
+
 def mps_from_dense(u: np.ndarray, n: int, order: str, eps: float, chi: int) -> list[np.ndarray]:
+    """TT-SVD (Eq. 8) of a dense field u[x, z] or u[x, y, z]."""
     u = _f64(u)
-    return _Mps(_load().oc_mps_from_dense(n, _ORDER[order], _dp(u), float(eps), int(chi))).cores()
+    return _Mps(_load().oc_mps_from_dense(_dims(u), n, _ORDER[order], _dp(u), float(eps), int(chi))).cores()
 
 
 def velocity_mps(c: np.ndarray, n: int, order: str, eps_c: float, chi_c: int) -> list[np.ndarray]:
@@ -192,25 +202,37 @@ def velocity_mps(c: np.ndarray, n: int, order: str, eps_c: float, chi_c: int) ->
     return mps_from_dense(c * c, n, order, eps_c, chi_c)
 
 
-def mps_to_dense(cores: list[np.ndarray], n: int, order: str) -> np.ndarray:
+def mps_to_dense(cores: list[np.ndarray], n: int, order: str, dims: int = 2) -> np.ndarray:
     N = 1 << n
-    out = np.zeros((N, N))
+    out = np.zeros((N,) * dims)
     A = _Mps.of(cores)
-    _load().oc_mps_to_dense(A.h, n, _ORDER[order], _dp(out))
+    _load().oc_mps_to_dense(A.h, dims, n, _ORDER[order], _dp(out))
     return out
 
 
 def mps_sample(cores: list[np.ndarray], n: int, order: str, ix, iz) -> np.ndarray:
-    ix = np.ascontiguousarray(np.atleast_1d(ix), dtype=np.int32)
-    iz = np.ascontiguousarray(np.atleast_1d(iz), dtype=np.int32)
-    out = np.zeros(ix.size)
+    """u at the points (ix[p], iz[p]) of a 2D grid."""
+    pts = np.stack([np.atleast_1d(ix), np.atleast_1d(iz)], axis=1)
+    return mps_sample_points(cores, n, order, pts)
+
+
+def mps_sample_points(cores: list[np.ndarray], n: int, order: str, pts) -> np.ndarray:
+    """u at each point of pts (np x dims)."""
+    pts = _pt(np.atleast_2d(pts))
+    out = np.zeros(pts.shape[0])
     A = _Mps.of(cores)
-    _load().oc_mps_sample(A.h, n, _ORDER[order], ix.size, _ip(ix), _ip(iz), _dp(out))
+    _load().oc_mps_sample(A.h, pts.shape[1], n, _ORDER[order], pts.shape[0], _ip(pts), _dp(out))
     return out
 
 
 def product_state(ix: int, iz: int, n: int, order: str) -> list[np.ndarray]:
-    return _Mps(_load().oc_product_state(n, _ORDER[order], int(ix), int(iz))).cores()
+    return point_state((ix, iz), n, order)
+
+
+def point_state(p, n: int, order: str) -> list[np.ndarray]:
+    """Rank-1 MPS of the unit impulse at the point p (2 or 3 coordinates)."""
+    p = _pt(p)
+    return _Mps(_load().oc_product_state(p.size, n, _ORDER[order], _ip(p))).cores()
 
 
 def tt_round(cores: list[np.ndarray], eps: float, chi: int) -> list[np.ndarray]:
@@ -225,42 +247,67 @@ def mps_sum(terms: list[tuple[float, list[np.ndarray]]]) -> list[np.ndarray]:
     return _Mps(_load().oc_sum(len(hs), _dp(coef), arr)).cores()
 
 
-def shift_mpo_2d(n: int, axis: str, sign: int, bc: str, order: str) -> list[np.ndarray]:
-    return _Mpo(_load().oc_shift_mpo(n, _AXIS[axis], int(sign), _BC[bc], _ORDER[order])).cores()
-
-
-def laplacian_mpo(n: int, order: str, bc: str) -> list[np.ndarray]:
-    return _Mpo(_load().oc_laplacian_mpo(n, _ORDER[order], _BC[bc])).cores()
-
-
-def laplacian_sum_of_shifts(n: int, order: str, bc: str) -> list[np.ndarray]:
-    return _Mpo(_load().oc_laplacian_sum_of_shifts(n, _ORDER[order], _BC[bc])).cores()
-
-
-def _mpo_handle(kind: str, n: int, order: str, bc: str) -> _Mpo:
+def _laplacian(kind: str, n: int, order: str, bc: str, dims: int) -> _Mpo:
     lib = _load()
     f = lib.oc_laplacian_mpo if kind == "laplacian" else lib.oc_laplacian_sum_of_shifts
-    return _Mpo(f(n, _ORDER[order], _BC[bc]))
+    return _Mpo(f(dims, n, _ORDER[order], _BC[bc]))
 
 
-def grid_operator(kind: str, n: int, order: str, bc: str, axis: str = "x", sign: int = 1) -> np.ndarray:
-    """(N^2 x N^2) matrix of one of the oracle's MPOs acting on u flattened as
-    x N + z: kind = 'laplacian' (five-state automaton), 'sum_of_shifts'
-    (Eq. 16 as the plain bond-9 sum) or 'shift' (axis, sign)."""
+def laplacian_mpo(n: int, order: str, bc: str, dims: int = 2) -> list[np.ndarray]:
+    return _laplacian("laplacian", n, order, bc, dims).cores()
+
+
+def laplacian_sum_of_shifts(n: int, order: str, bc: str, dims: int = 2) -> list[np.ndarray]:
+    return _laplacian("sum_of_shifts", n, order, bc, dims).cores()
+
+
+def shift_mpo(n: int, axis: str, sign: int, bc: str, order: str, dims: int = 2) -> list[np.ndarray]:
+    return _Mpo(_load().oc_shift_mpo(dims, n, _ORDER[order], _axis(axis, dims), int(sign), _BC[bc])).cores()
+
+
+def _axis(axis: str, dims: int) -> int:
+    return {"x": 0, "y": 1, "z": dims - 1}[axis]
+
+
+def grid_operator(kind: str, n: int, order: str, bc: str, axis: str = "x", sign: int = 1,
+                  dims: int = 2) -> np.ndarray:
+    """(N^dims x N^dims) matrix of one of the oracle's MPOs acting on the
+    dense field flattened in its layout: kind = 'laplacian' (the automaton),
+    'sum_of_shifts' (Eq. 16 as the plain sum) or 'shift' (axis, sign)."""
     lib = _load()
     if kind == "shift":
-        W = _Mpo(lib.oc_shift_mpo(n, _AXIS[axis], int(sign), _BC[bc], _ORDER[order]))
+        W = _Mpo(lib.oc_shift_mpo(dims, n, _ORDER[order], _axis(axis, dims), int(sign), _BC[bc]))
     else:
-        W = _mpo_handle(kind, n, order, bc)
-    NN = 1 << (2 * n)
-    out = np.zeros((NN, NN))
-    lib.oc_mpo_grid_operator(W.h, n, _ORDER[order], _dp(out))
+        W = _laplacian(kind, n, order, bc, dims)
+    P = 1 << (dims * n)
+    out = np.zeros((P, P))
+    lib.oc_mpo_grid_operator(W.h, dims, n, _ORDER[order], _dp(out))
     return out
+
+
+def a_operator_grid(n: int, order: str, bc: str, c2: list[np.ndarray], lambda2: float) -> np.ndarray:
+    """(N^2 x N^2) matrix of the oracle's MPO of Eq. 7, A = 2I + lambda^2 C^2 L."""
+    lib = _load()
+    L = _laplacian("laplacian", n, order, bc, 2)
+    C2 = _Mps.of(c2)
+    A = _Mpo(lib.oc_a_operator_mpo(L.h, C2.h, float(lambda2)))
+    P = 1 << (2 * n)
+    out = np.zeros((P, P))
+    lib.oc_mpo_grid_operator(A.h, 2, n, _ORDER[order], _dp(out))
+    return out
+
+
+def a_operator_bonds(n: int, order: str, bc: str, c2: list[np.ndarray], lambda2: float) -> list[int]:
+    lib = _load()
+    L = _laplacian("laplacian", n, order, bc, 2)
+    C2 = _Mps.of(c2)
+    A = _Mpo(lib.oc_a_operator_mpo(L.h, C2.h, float(lambda2)))
+    return [1] + [int(w.shape[3]) for w in A.cores()]
 
 
 def zipup_lr_laplacian(n: int, order: str, bc: str, A: list[np.ndarray], eps: float, chi: int) -> list[np.ndarray]:
     """Zip-up of the oracle's own Laplacian MPO with A, sites 1 -> d."""
-    W = _mpo_handle("laplacian", n, order, bc)
+    W = _laplacian("laplacian", n, order, bc, 2)
     B = _Mps.of(A)
     return _Mps(_load().oc_zipup_lr(W.h, B.h, float(eps), int(chi))).cores()
 
@@ -274,26 +321,50 @@ def zipup_rl_diagonal(c2: list[np.ndarray], A: list[np.ndarray], eps: float, chi
     return _Mps(lib.oc_zipup_rl(W.h, B.h, float(eps), int(chi))).cores()
 
 
+def _src(src, dims):
+    if src is None:
+        return None, None
+    p = _pt(src)
+    assert p.size == dims
+    return p, _ip(p)
+
+
 def mps_step(n: int, order: str, bc: str, c2: list[np.ndarray], lambda2: float, prev: list[np.ndarray],
-             cur: list[np.ndarray], eps: float, chi: int, src: tuple[int, int] | None = None,
-             amp: float = 0.0) -> list[np.ndarray]:
-    """One step of Eq. 17 with the oracle's own Laplacian MPO (Eq. 16)."""
+             cur: list[np.ndarray], eps: float, chi: int, src=None, amp: float = 0.0,
+             dims: int = 2) -> list[np.ndarray]:
+    """One step of Eq. 17 with the oracle's own Laplacian MPO (Eq. 16; the
+    7-point operator when dims = 3)."""
     lib = _load()
-    L = _mpo_handle("laplacian", n, order, bc)
-    sx, sz = (-1, -1) if src is None else (int(src[0]), int(src[1]))
+    L = _laplacian("laplacian", n, order, bc, dims)
     C2, P, Q = _Mps.of(c2), _Mps.of(prev), _Mps.of(cur)  # held until the call returns
-    h = lib.oc_step(L.h, C2.h, float(lambda2), P.h, Q.h, float(eps), int(chi), sx, sz, float(amp), n,
+    keep, sp = _src(src, dims)
+    h = lib.oc_step(L.h, C2.h, float(lambda2), P.h, Q.h, float(eps), int(chi), sp, float(amp), dims, n,
                     _ORDER[order])
     return _Mps(h).cores()
 
 
+def mps_step_fused(n: int, order: str, bc: str, c2: list[np.ndarray], lambda2: float, prev: list[np.ndarray],
+                   cur: list[np.ndarray], eps: float, chi: int, src=None, amp: float = 0.0) -> list[np.ndarray]:
+    """The step of Eq. 7 with A = 2I + lambda^2 C^2 L applied as one MPO."""
+    lib = _load()
+    L = _laplacian("laplacian", n, order, bc, 2)
+    C2, P, Q = _Mps.of(c2), _Mps.of(prev), _Mps.of(cur)
+    A = _Mpo(lib.oc_a_operator_mpo(L.h, C2.h, float(lambda2)))
+    keep, sp = _src(src, 2)
+    h = lib.oc_step_fused(A.h, P.h, Q.h, float(eps), int(chi), sp, float(amp), 2, n, _ORDER[order])
+    return _Mps(h).cores()
+
+
 def fdtd_step(u_prev: np.ndarray, u_cur: np.ndarray, c2: np.ndarray, lambda2: float, bc: str,
-              src: tuple[int, int] | None = None, amp: float = 0.0) -> np.ndarray:
+              src=None, amp: float = 0.0) -> np.ndarray:
+    """Eq. 2 (the 7-point stencil for a 3D field)."""
     u_prev, u_cur, c2 = _f64(u_prev), _f64(u_cur), _f64(c2)
-    N = u_cur.shape[0]
-    out = np.zeros((N, N))
-    sx, sz = (-1, -1) if src is None else (int(src[0]), int(src[1]))
-    _load().oc_fdtd_step(N, _dp(u_prev), _dp(u_cur), _dp(c2), float(lambda2), _BC[bc], sx, sz, float(amp), _dp(out))
+    dims = _dims(u_cur)
+    n = int(u_cur.shape[0]).bit_length() - 1
+    out = np.zeros(u_cur.shape)
+    keep, sp = _src(src, dims)
+    _load().oc_fdtd_step(dims, n, _dp(u_prev), _dp(u_cur), _dp(c2), float(lambda2), _BC[bc], sp, float(amp),
+                         _dp(out))
     return out
 
 

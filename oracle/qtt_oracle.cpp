@@ -12,11 +12,17 @@
 // Paper: "Quantum Circuit and Tensor Network Implementation of the 2D
 // Acoustic Wave Equation" (Nemeth & Vattay).
 //
+// Besides the 2D step it covers the transition operator of Eq. 7 as one
+// MPO and the fused step, and the 3D extension of Sec. 6 (three registers,
+// the 7-point Laplacian).
+//
 // Conventions (the readings of the paper are those of the numpy oracle):
-//   * dense fields u[x * N + z], N = 2^n, x horizontal, z depth (Sec. 2, Eq. 2);
-//   * d = 2n binary sites in the tensor-product order of Eq. 12 (least
-//     significant bit first); order 0 = SEQUENTIAL (x register, then z
-//     register, Eq. 14-15), order 1 = INTERLEAVED (x_0, z_0, x_1, z_1, ...);
+//   * dense fields u[x * N + z], N = 2^n, x horizontal, z depth (Sec. 2,
+//     Eq. 2); in 3D u[(x * N + y) * N + z];
+//   * d = dims * n binary sites in the tensor-product order of Eq. 12 (least
+//     significant bit first); order 0 = SEQUENTIAL (one register after the
+//     other, Eq. 14-15), order 1 = INTERLEAVED (x_0, z_0, x_1, z_1, ...; in
+//     3D x_0, y_0, z_0, x_1, ...);
 //   * boundary 0 = PERIODIC (the wrap the text states, Sec. 3.1), 1 = ZERO
 //     (Eq. 11 as printed: the overflow carry is dropped);
 //   * MPS core k: [r_{k-1}][2][r_k], row-major (Eq. 8); MPO core k:
@@ -60,17 +66,28 @@ Mat transpose(const Mat& A) {
 // the sign opposite to the leading entry (no cancellation); Q is formed by
 // applying the reflectors, last first, to the first k columns of I_m
 // (Golub & Van Loan, Algorithms 5.1.1-5.1.2 in spirit, written for clarity).
+// The reflector is built from the column divided by its largest entry (the
+// reflection depends only on the direction): squares of entries near the
+// underflow threshold would otherwise vanish and leave it non-orthogonal.
 void householder_qr(const Mat& A, Mat& Q, Mat& R) {
     const int m = A.m, n = A.n, k = std::min(m, n);
     Mat W = A;
     std::vector<std::vector<double>> refl(k);
     std::vector<double> vnorm2(k, 0.0);
     for (int j = 0; j < k; ++j) {
+        double sc = 0.0;
+        for (int i = j; i < m; ++i) sc = std::max(sc, std::fabs(W(i, j)));
+        std::vector<double> v(m - j, 0.0);
+        if (sc == 0.0) {  // nothing to annihilate: identity reflector
+            refl[j] = std::move(v);
+            continue;
+        }
         double nx = 0.0;
-        for (int i = j; i < m; ++i) nx += W(i, j) * W(i, j);
+        for (int i = j; i < m; ++i) {
+            v[i - j] = W(i, j) / sc;
+            nx += v[i - j] * v[i - j];
+        }
         nx = std::sqrt(nx);
-        std::vector<double> v(m - j);
-        for (int i = j; i < m; ++i) v[i - j] = W(i, j);
         const double alpha = v[0] >= 0.0 ? -nx : nx;
         v[0] -= alpha;
         double vv = 0.0;
@@ -103,13 +120,26 @@ void householder_qr(const Mat& A, Mat& Q, Mat& R) {
     }
 }
 
+// Euclidean norm of x[0..m) computed on x / max|x_i|, so that squares of
+// entries near the underflow (or overflow) threshold do not vanish (blow up).
+double norm_scaled(const std::vector<double>& x) {
+    double sc = 0.0;
+    for (double v : x) sc = std::max(sc, std::fabs(v));
+    if (sc == 0.0) return 0.0;
+    double s2 = 0.0;
+    for (double v : x) s2 += (v / sc) * (v / sc);
+    return sc * std::sqrt(s2);
+}
+
 // One-sided Jacobi SVD (Hestenes; de Rijk's cyclic order), M (m x n) =
 // U (m x p) diag(S) Vt (p x n), p = min(m, n), S descending.
 // Works on the columns of M, or of M^T when M is wide: each pair (p, q) of
 // columns is rotated so that the two become orthogonal, with the smaller of
 // the two rotation angles, until a whole sweep finds every pair orthogonal
-// to m * DBL_EPSILON relative to its norms.  The singular values are the
-// final column norms.  Returns the sweep count, or -1 after 80 sweeps.
+// to m * DBL_EPSILON (the cosine of the angle between them, computed on the
+// normalised columns).  A rotation too small to change a column in FP64 is
+// not counted.  The singular values are the final column norms.  Returns
+// the sweep count, or -1 after 80 sweeps.
 int jacobi_svd(const Mat& M, Mat& U, std::vector<double>& S, Mat& Vt) {
     const bool wide = M.m < M.n;
     const Mat A = wide ? transpose(M) : M;  // rows >= cols
@@ -128,19 +158,20 @@ int jacobi_svd(const Mat& M, Mat& U, std::vector<double>& S, Mat& Vt) {
         bool rotated = false;
         for (int p = 0; p < n - 1; ++p)
             for (int q = p + 1; q < n; ++q) {
-                double alpha = 0.0, beta = 0.0, gamma = 0.0;
-                for (int i = 0; i < m; ++i) {
-                    alpha += col[p][i] * col[p][i];
-                    beta += col[q][i] * col[q][i];
-                    gamma += col[p][i] * col[q][i];
-                }
-                if (gamma == 0.0 || std::fabs(gamma) <= tol * std::sqrt(alpha * beta)) continue;
-                rotated = true;
+                const double np_ = norm_scaled(col[p]), nq_ = norm_scaled(col[q]);
+                if (np_ == 0.0 || nq_ == 0.0) continue;
+                double rho = 0.0;  // cosine of the angle between the two columns
+                for (int i = 0; i < m; ++i) rho += (col[p][i] / np_) * (col[q][i] / nq_);
+                if (std::fabs(rho) <= tol) continue;
                 // [c_p, c_q] <- [c_p, c_q] [[c, s], [-s, c]] zeroes the cross
-                // product when t = s / c solves t^2 + 2 zeta t - 1 = 0.
-                const double zeta = (beta - alpha) / (2.0 * gamma);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                // product when t = s / c solves t^2 + 2 zeta t - 1 = 0, with
+                // zeta = (|c_q|^2 - |c_p|^2) / (2 c_p . c_q)
+                const double zeta = (nq_ / np_ - np_ / nq_) / (2.0 * rho);
+                // (hypot: zeta reaches 1e160 and more for columns of very different size)
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::hypot(1.0, zeta));
                 const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                if (s == 0.0) continue;
+                rotated = true;
                 for (int i = 0; i < m; ++i) {
                     const double xp = col[p][i], xq = col[q][i];
                     col[p][i] = c * xp - s * xq;
@@ -155,11 +186,7 @@ int jacobi_svd(const Mat& M, Mat& U, std::vector<double>& S, Mat& Vt) {
         converged = !rotated;
     }
     std::vector<double> norm(n);
-    for (int j = 0; j < n; ++j) {
-        double s2 = 0.0;
-        for (int i = 0; i < m; ++i) s2 += col[j][i] * col[j][i];
-        norm[j] = std::sqrt(s2);
-    }
+    for (int j = 0; j < n; ++j) norm[j] = norm_scaled(col[j]);
     std::vector<int> perm(n);
     std::iota(perm.begin(), perm.end(), 0);
     std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return norm[a] > norm[b]; });
@@ -236,27 +263,46 @@ using Mpo = std::vector<OpCore>;
 // ---------------------------------------------------------------------------
 // Register encoding (Sec. 3 Eq. 3; Sec. 4.2 Eq. 12, Eq. 14-15)
 // ---------------------------------------------------------------------------
-// Axis (0 = x, 1 = z) and bit carried by site k.
-void site_axis(int n, int order, int k, int& axis, int& bit) {
-    if (order == 0) {
-        axis = k < n ? 0 : 1;
-        bit = k < n ? k : k - n;
+// A grid of dims axes (2: x, z; 3: x, y, z for the extension of Sec. 6),
+// N = 2^n points per axis, d = dims * n sites.  Dense fields are indexed by
+// the point's coordinates in axis order, the last fastest: u[x N + z] in 2D,
+// u[(x N + y) N + z] in 3D.
+struct Grid {
+    int dims = 2, n = 1, order = 1;
+    int d() const { return dims * n; }
+    int N() const { return 1 << n; }
+    int64_t points() const { return (int64_t)1 << (dims * n); }
+};
+
+// Axis and bit carried by site k: least significant bit first per axis
+// (Eq. 12); SEQUENTIAL puts the registers one after another (Eq. 14-15),
+// INTERLEAVED takes bit b of every axis before bit b+1.
+void site_axis(const Grid& g, int k, int& axis, int& bit) {
+    if (g.order == 0) {
+        axis = k / g.n;
+        bit = k % g.n;
     } else {
-        axis = k & 1;
-        bit = k >> 1;
+        axis = k % g.dims;
+        bit = k / g.dims;
     }
 }
 
-// Flat index of grid point (x, z) in the order-d tensor, site 1 most
-// significant (the row-major reshapes of Eq. 8).
-int64_t site_index(int n, int order, int x, int z) {
-    const int d = 2 * n;
+// Coordinates of the point with dense index lin.
+void coords(const Grid& g, int64_t lin, int* p) {
+    for (int a = g.dims - 1; a >= 0; --a) {
+        p[a] = (int)(lin % g.N());
+        lin /= g.N();
+    }
+}
+
+// Flat index of a point in the order-d tensor, site 1 most significant (the
+// row-major reshapes of Eq. 8).
+int64_t site_index(const Grid& g, const int* p) {
     int64_t idx = 0;
-    for (int k = 0; k < d; ++k) {
+    for (int k = 0; k < g.d(); ++k) {
         int axis, bit;
-        site_axis(n, order, k, axis, bit);
-        const int s = ((axis == 0 ? x : z) >> bit) & 1;
-        idx = idx * 2 + s;
+        site_axis(g, k, axis, bit);
+        idx = idx * 2 + ((p[axis] >> bit) & 1);
     }
     return idx;
 }
@@ -291,12 +337,14 @@ Mps tt_svd(const std::vector<double>& t, int d, double eps, int chi) {
     return cores;
 }
 
-Mps mps_from_dense(const double* u, int n, int order, double eps, int chi) {
-    const int N = 1 << n, d = 2 * n;
-    std::vector<double> t((size_t)1 << d);
-    for (int x = 0; x < N; ++x)
-        for (int z = 0; z < N; ++z) t[site_index(n, order, x, z)] = u[(size_t)x * N + z];
-    return tt_svd(t, d, eps, chi);
+Mps mps_from_dense(const Grid& g, const double* u, double eps, int chi) {
+    std::vector<double> t((size_t)g.points());
+    int p[3];
+    for (int64_t lin = 0; lin < g.points(); ++lin) {
+        coords(g, lin, p);
+        t[site_index(g, p)] = u[lin];
+    }
+    return tt_svd(t, g.d(), eps, chi);
 }
 
 // Contraction of all cores (Eq. 8 summed over the bonds), site 1 most significant.
@@ -319,20 +367,22 @@ std::vector<double> mps_full(const Mps& A) {
     return v;
 }
 
-void mps_to_dense(const Mps& A, int n, int order, double* u) {
-    const int N = 1 << n;
+void mps_to_dense(const Grid& g, const Mps& A, double* u) {
     const std::vector<double> t = mps_full(A);
-    for (int x = 0; x < N; ++x)
-        for (int z = 0; z < N; ++z) u[(size_t)x * N + z] = t[site_index(n, order, x, z)];
+    int p[3];
+    for (int64_t lin = 0; lin < g.points(); ++lin) {
+        coords(g, lin, p);
+        u[lin] = t[site_index(g, p)];
+    }
 }
 
-// u(x, z) = A^(1)_{s_1} ... A^(d)_{s_d} (Eq. 8).
-double mps_sample(const Mps& A, int n, int order, int x, int z) {
+// u(p) = A^(1)_{s_1} ... A^(d)_{s_d} (Eq. 8).
+double mps_sample(const Grid& g, const Mps& A, const int* p) {
     std::vector<double> v(1, 1.0);
-    for (int k = 0; k < 2 * n; ++k) {
+    for (int k = 0; k < g.d(); ++k) {
         int axis, bit;
-        site_axis(n, order, k, axis, bit);
-        const int s = ((axis == 0 ? x : z) >> bit) & 1;
+        site_axis(g, k, axis, bit);
+        const int s = (p[axis] >> bit) & 1;
         const Core& c = A[k];
         std::vector<double> nv(c.r, 0.0);
         for (int b = 0; b < c.l; ++b)
@@ -342,14 +392,14 @@ double mps_sample(const Mps& A, int n, int order, int x, int z) {
     return v[0];
 }
 
-// Rank-1 MPS of the unit impulse at (x, z): one-hot cores of its bits.
-Mps product_state(int n, int order, int x, int z) {
+// Rank-1 MPS of the unit impulse at p: one-hot cores of its bits.
+Mps product_state(const Grid& g, const int* p) {
     Mps out;
-    for (int k = 0; k < 2 * n; ++k) {
+    for (int k = 0; k < g.d(); ++k) {
         int axis, bit;
-        site_axis(n, order, k, axis, bit);
+        site_axis(g, k, axis, bit);
         Core c(1, 1);
-        c.at(0, ((axis == 0 ? x : z) >> bit) & 1, 0) = 1.0;
+        c.at(0, (p[axis] >> bit) & 1, 0) = 1.0;
         out.push_back(c);
     }
     return out;
@@ -358,22 +408,21 @@ Mps product_state(int n, int order, int x, int z) {
 // ---------------------------------------------------------------------------
 // Shift and Laplacian MPOs (Sec. 3.1 Eq. 5-6; Sec. 4.2 Eq. 9-16)
 // ---------------------------------------------------------------------------
-// 2D shift S_axis^{sign} (Eq. 14-15) in the chosen order.  The bond carries
-// the carry (sign +1) or borrow (sign -1) of the increment along the axis'
-// bits, least significant first (Eq. 9 / Eq. 13: with no incoming carry the
-// bit is copied; with a carry, bit 0 -> 1 absorbs it and bit 1 -> 0 passes
-// it on; a borrow the other way round).  The first site of the axis injects
-// carry 1 (Eq. 10); sites of the other axis pass the carry through on
+// Shift S_axis^{sign} lifted to the grid (Eq. 14-15).  The bond carries the
+// carry (sign +1) or borrow (sign -1) of the increment along the axis' bits,
+// least significant first (Eq. 9 / Eq. 13: with no incoming carry the bit
+// is copied; with a carry, bit 0 -> 1 absorbs it and bit 1 -> 0 passes it
+// on; a borrow the other way round).  The first site of the axis injects
+// carry 1 (Eq. 10); sites of other axes pass the carry through on
 // identities; after the axis' last site the outgoing carry is summed over
 // (periodic wrap) or only carry 0 is kept (Eq. 11, zero outside the grid).
-Mpo shift_mpo(int n, int axis_sel, int sign, int bc, int order) {
-    const int d = 2 * n;
+Mpo shift_mpo(const Grid& g, int axis_sel, int sign, int bc) {
     Mpo W;
     int carry_in = 1;  // bond dimension to the left of the current site
     int seen = 0;      // sites of the axis already passed
-    for (int k = 0; k < d; ++k) {
+    for (int k = 0; k < g.d(); ++k) {
         int axis, bit;
-        site_axis(n, order, k, axis, bit);
+        site_axis(g, k, axis, bit);
         if (axis != axis_sel) {
             OpCore c(carry_in, carry_in);
             for (int a = 0; a < carry_in; ++a)
@@ -381,7 +430,7 @@ Mpo shift_mpo(int n, int axis_sel, int sign, int bc, int order) {
             W.push_back(c);
             continue;
         }
-        const bool first = (seen == 0), last = (seen == n - 1);
+        const bool first = (seen == 0), last = (seen == g.n - 1);
         ++seen;
         // full carry table T[a_in][t][s][a_out], a in {0, 1}
         double T[2][2][2][2] = {};
@@ -452,59 +501,65 @@ Mpo mpo_sum(const std::vector<double>& coef, const std::vector<Mpo>& terms) {
     return out;
 }
 
-// Eq. 16 as the plain sum of the four lifted shifts and -4I (bond 9); used
-// to pin the five-state form below.
-Mpo laplacian_sum_of_shifts(int n, int order, int bc) {
-    std::vector<Mpo> terms = {shift_mpo(n, 0, +1, bc, order), shift_mpo(n, 0, -1, bc, order),
-                              shift_mpo(n, 1, +1, bc, order), shift_mpo(n, 1, -1, bc, order),
-                              identity_mpo(2 * n)};
-    return mpo_sum({1.0, 1.0, 1.0, 1.0, -4.0}, terms);
+// Eq. 16 (Eq. 6 with a third pair of shifts in 3D) as the plain sum of the
+// lifted shifts and -2 dims I (bond 4 dims + 1); used to pin the automaton.
+Mpo laplacian_sum_of_shifts(const Grid& g, int bc) {
+    std::vector<Mpo> terms;
+    std::vector<double> coef;
+    for (int a = 0; a < g.dims; ++a)
+        for (int sign : {+1, -1}) {
+            terms.push_back(shift_mpo(g, a, sign, bc));
+            coef.push_back(1.0);
+        }
+    terms.push_back(identity_mpo(g.d()));
+    coef.push_back(-2.0 * g.dims);
+    return mpo_sum(coef, terms);
 }
 
-// Eq. 16 as one carry automaton with five bond states: D (nothing pending,
-// identity from here on), XP / XM (an x increment / decrement still
-// carrying), ZP / ZM (the same for z).  The left boundary weighs D by -4
-// and each shift state by 1 (every shift starts with its carry, Eq. 10); at
-// a site of axis a the pending state AP copies nothing: bit 1 -> 0 keeps it
-// pending, bit 0 -> 1 resolves it to D; AM the other way round; states of
-// the other axis pass by identity, D stays D.  The right boundary accepts
-// every state (periodic) or only D (zero, Eq. 11).  Bond states that are
-// zero on either side are removed, until no bond shrinks.  This is the
-// gauge of the MPO the zip-up truncates in, which the step's result
-// depends on.
-Mpo laplacian_mpo(int n, int order, int bc) {
-    const int d = 2 * n;
-    enum { D = 0, XP = 1, XM = 2, ZP = 3, ZM = 4 };
+// Eq. 16 as one carry automaton with 2 dims + 1 bond states: D (nothing
+// pending, identity from here on) and, per axis a, P_a / M_a (an increment /
+// decrement along a still carrying).  The left boundary weighs D by -2 dims
+// (-4 in 2D) and each shift state by 1 (every shift starts with its carry,
+// Eq. 10); at a site of axis a, P_a keeps pending on bit 1 -> 0 and
+// resolves to D on bit 0 -> 1, M_a the other way round; states of other
+// axes pass by identity, D stays D.  The right boundary accepts every state
+// (periodic) or only D (zero, Eq. 11).  Bond states that are zero on either
+// side are removed, until no bond shrinks.  This is the gauge of the MPO the
+// zip-up truncates in, which the step's result depends on.
+Mpo laplacian_mpo(const Grid& g, int bc) {
+    const int d = g.d(), ns = 2 * g.dims + 1, D = 0;
     std::vector<OpCore> W;
     for (int k = 0; k < d; ++k) {
         int axis, bit;
-        site_axis(n, order, k, axis, bit);
-        OpCore c(5, 5);
-        const int p = axis == 0 ? XP : ZP, m = axis == 0 ? XM : ZM;
-        const int op = axis == 0 ? ZP : XP, om = axis == 0 ? ZM : XM;
-        for (int s = 0; s < 2; ++s) {
-            c.at(D, s, s, D) = 1.0;
-            c.at(op, s, s, op) = 1.0;
-            c.at(om, s, s, om) = 1.0;
+        site_axis(g, k, axis, bit);
+        OpCore c(ns, ns);
+        for (int s = 0; s < 2; ++s) c.at(D, s, s, D) = 1.0;
+        for (int a = 0; a < g.dims; ++a) {
+            const int p = 1 + 2 * a, m = 2 + 2 * a;
+            if (a != axis) {
+                for (int s = 0; s < 2; ++s) c.at(p, s, s, p) = c.at(m, s, s, m) = 1.0;
+                continue;
+            }
+            c.at(p, 0, 1, p) = 1.0;  // increment: 1 -> 0, still carrying
+            c.at(p, 1, 0, D) = 1.0;  // increment: 0 -> 1, done
+            c.at(m, 1, 0, m) = 1.0;  // decrement: 0 -> 1, still borrowing
+            c.at(m, 0, 1, D) = 1.0;  // decrement: 1 -> 0, done
         }
-        c.at(p, 0, 1, p) = 1.0;  // increment: 1 -> 0, still carrying
-        c.at(p, 1, 0, D) = 1.0;  // increment: 0 -> 1, done
-        c.at(m, 1, 0, m) = 1.0;  // decrement: 0 -> 1, still borrowing
-        c.at(m, 0, 1, D) = 1.0;  // decrement: 1 -> 0, done
         W.push_back(c);
     }
-    const double inject[5] = {-4.0, 1.0, 1.0, 1.0, 1.0};
-    OpCore first(1, 5);
-    for (int a = 0; a < 5; ++a)
+    std::vector<double> inject(ns, 1.0);
+    inject[D] = -2.0 * g.dims;
+    OpCore first(1, ns);
+    for (int a = 0; a < ns; ++a)
         for (int t = 0; t < 2; ++t)
             for (int s = 0; s < 2; ++s)
-                for (int b = 0; b < 5; ++b) first.at(0, t, s, b) += inject[a] * W[0].at(a, t, s, b);
+                for (int b = 0; b < ns; ++b) first.at(0, t, s, b) += inject[a] * W[0].at(a, t, s, b);
     W[0] = first;
     OpCore lastc(W[d - 1].l, 1);
     for (int a = 0; a < W[d - 1].l; ++a)
         for (int t = 0; t < 2; ++t)
             for (int s = 0; s < 2; ++s)
-                for (int b = 0; b < 5; ++b)
+                for (int b = 0; b < ns; ++b)
                     if (bc == 0 || b == D) lastc.at(a, t, s, 0) += W[d - 1].at(a, t, s, b);
     W[d - 1] = lastc;
     bool changed = true;
@@ -539,7 +594,6 @@ Mpo laplacian_mpo(int n, int order, int bc) {
     }
     return W;
 }
-
 // Sec. 4.3: the diagonal MPO of an MPS, W[r][t][s][r'] = delta_{ts} B[r][s][r'].
 Mpo diagonal_mpo(const Mps& B) {
     Mpo W;
@@ -740,65 +794,144 @@ Mps tt_round(Mps A, double eps, int chi) {
 // One time step of Eq. 17 in MPS form:
 //   phi = L psi^k (zip-up, sites 1 -> d); eta = C^2 phi (zip-up of diag(c^2),
 //   sites d -> 1); theta = 2 psi^k - psi^{k-1} + lambda^2 eta [+ amp e_src];
-//   psi^{k+1} = round(theta).
-Mps mps_step(const Mpo& L, const Mps& c2, double lambda2, const Mps& prev, const Mps& cur, double eps, int chi,
-             int sx, int sz, double amp, int n, int order) {
+//   psi^{k+1} = round(theta).  src: the source point, or null.
+Mps mps_step(const Grid& g, const Mpo& L, const Mps& c2, double lambda2, const Mps& prev, const Mps& cur, double eps,
+             int chi, const int* src, double amp) {
     const Mps phi = zipup_lr(L, cur, eps, chi);
     const Mps eta = zipup_rl(diagonal_mpo(c2), phi, eps, chi);
     std::vector<double> coef = {2.0, -1.0, lambda2};
     std::vector<const Mps*> terms = {&cur, &prev, &eta};
-    Mps src;
-    if (sx >= 0) {
-        src = product_state(n, order, sx, sz);
+    Mps e;
+    if (src) {
+        e = product_state(g, src);
         coef.push_back(amp);
-        terms.push_back(&src);
+        terms.push_back(&e);
     }
     return tt_round(mps_sum(coef, terms), eps, chi);
 }
 
-// Operator matrix of an MPO on the dense grid, out[(x N + z) * N^2 + (x' N + z')].
-void mpo_grid_operator(const Mpo& W, int n, int order, double* out) {
-    const int N = 1 << n, d = 2 * n;
-    const int64_t NN = (int64_t)N * N;
-    for (int64_t p = 0; p < NN; ++p)
-        for (int64_t q = 0; q < NN; ++q) {
-            const int xo = (int)(p / N), zo = (int)(p % N), xi = (int)(q / N), zi = (int)(q % N);
+// ---------------------------------------------------------------------------
+// The transition operator of Eq. 7 as one MPO: A = 2I + lambda^2 C^2 L
+// ---------------------------------------------------------------------------
+// Operator product W_out W_in (W_in acts first): core k is
+// sum_u W_out[a][t][u][a'] W_in[b][u][s][b'] on the bond pairs (a, b).
+Mpo mpo_product(const Mpo& Wout, const Mpo& Win) {
+    Mpo out;
+    for (size_t k = 0; k < Wout.size(); ++k) {
+        const OpCore &A = Wout[k], &B = Win[k];
+        OpCore P(A.l * B.l, A.r * B.r);
+        for (int a = 0; a < A.l; ++a)
+            for (int b = 0; b < B.l; ++b)
+                for (int t = 0; t < 2; ++t)
+                    for (int s = 0; s < 2; ++s)
+                        for (int a2 = 0; a2 < A.r; ++a2)
+                            for (int b2 = 0; b2 < B.r; ++b2) {
+                                double v = 0.0;
+                                for (int u = 0; u < 2; ++u) v += A.at(a, t, u, a2) * B.at(b, u, s, b2);
+                                P.at(a * B.l + b, t, s, a2 * B.r + b2) = v;
+                            }
+        out.push_back(P);
+    }
+    return out;
+}
+
+// A = 2I + lambda^2 C^2 L (Eq. 7): the diagonal MPO of c^2 times the
+// Laplacian MPO, plus twice the identity (bond r_c w + 1).  The paper gives
+// no representation; the reading shared with the library: the norm nu of the
+// last c^2 core (which holds the whole norm of c^2 after TT-SVD) moves into
+// the coefficient, lambda^2 nu, so that the two terms are of comparable size
+// at every cut the zip-up makes.  The operator is unchanged.
+Mpo a_operator_mpo(const Mpo& L, const Mps& c2, double lambda2) {
+    Mps B = c2;
+    double nu = 0.0;
+    for (double x : B.back().a) nu += x * x;
+    nu = std::sqrt(nu);
+    if (nu > 0.0) {
+        for (double& x : B.back().a) x /= nu;
+    } else {
+        nu = 1.0;
+    }
+    return mpo_sum({lambda2 * nu, 2.0}, {mpo_product(diagonal_mpo(B), L), identity_mpo((int)L.size())});
+}
+
+// The step of Eq. 7 with A applied as one operator: phi = A psi^k (zip-up,
+// sites 1 -> d); theta = phi - psi^{k-1} [+ amp e_src]; psi^{k+1} =
+// round(theta).  Exactly the step of mps_step; the truncation points differ.
+Mps mps_step_fused(const Grid& g, const Mpo& A, const Mps& prev, const Mps& cur, double eps, int chi, const int* src,
+                   double amp) {
+    const Mps phi = zipup_lr(A, cur, eps, chi);
+    std::vector<double> coef = {1.0, -1.0};
+    std::vector<const Mps*> terms = {&phi, &prev};
+    Mps e;
+    if (src) {
+        e = product_state(g, src);
+        coef.push_back(amp);
+        terms.push_back(&e);
+    }
+    return tt_round(mps_sum(coef, terms), eps, chi);
+}
+
+// Operator matrix of an MPO on the dense grid: out[p * P + q] = <p|W|q>,
+// P = N^dims points, p and q dense indices.
+void mpo_grid_operator(const Grid& g, const Mpo& W, double* out) {
+    const int64_t P = g.points();
+    int po[3], pi[3];
+    for (int64_t p = 0; p < P; ++p) {
+        coords(g, p, po);
+        for (int64_t q = 0; q < P; ++q) {
+            coords(g, q, pi);
             std::vector<double> v(1, 1.0);
-            for (int k = 0; k < d && !v.empty(); ++k) {
+            for (int k = 0; k < g.d(); ++k) {
                 int axis, bit;
-                site_axis(n, order, k, axis, bit);
-                const int t = ((axis == 0 ? xo : zo) >> bit) & 1, s = ((axis == 0 ? xi : zi) >> bit) & 1;
+                site_axis(g, k, axis, bit);
+                const int t = (po[axis] >> bit) & 1, s = (pi[axis] >> bit) & 1;
                 std::vector<double> nv(W[k].r, 0.0);
                 for (int a = 0; a < W[k].l; ++a)
                     for (int b = 0; b < W[k].r; ++b) nv[b] += v[a] * W[k].at(a, t, s, b);
                 v.swap(nv);
             }
-            out[p * NN + q] = v[0];
+            out[p * P + q] = v[0];
         }
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Dense FDTD (Sec. 2, Eq. 2)
+// Dense FDTD (Sec. 2, Eq. 2; the 7-point stencil in 3D)
 // ---------------------------------------------------------------------------
-void fdtd_step(int N, const double* prev, const double* cur, const double* c2, double lambda2, int bc, int sx, int sz,
-               double amp, double* out) {
-    auto at = [&](int x, int z) -> double {
-        if (bc == 0) return cur[(size_t)((x + N) % N) * N + (z + N) % N];
-        if (x < 0 || x >= N || z < 0 || z >= N) return 0.0;
-        return cur[(size_t)x * N + z];
-    };
-    for (int x = 0; x < N; ++x)
-        for (int z = 0; z < N; ++z) {
-            const size_t i = (size_t)x * N + z;
-            const double lap = at(x + 1, z) + at(x - 1, z) + at(x, z + 1) + at(x, z - 1) - 4.0 * cur[i];
-            out[i] = 2.0 * cur[i] - prev[i] + lambda2 * c2[i] * lap;
-        }
-    if (sx >= 0) out[(size_t)sx * N + sz] += amp;
+// u^{k+1} = 2 u^k - u^{k-1} + lambda^2 c^2 (sum of the 2 dims face
+// neighbours - 2 dims u^k), neighbours by the boundary rule (periodic wrap
+// or zero outside), plus amp at the source point (src may be null).
+void fdtd_step(const Grid& g, const double* prev, const double* cur, const double* c2, double lambda2, int bc,
+               const int* src, double amp, double* out) {
+    const int N = g.N();
+    int p[3], q[3];
+    for (int64_t lin = 0; lin < g.points(); ++lin) {
+        coords(g, lin, p);
+        double nb = 0.0;
+        for (int a = 0; a < g.dims; ++a)
+            for (int step : {+1, -1}) {
+                for (int b = 0; b < g.dims; ++b) q[b] = p[b];
+                q[a] += step;
+                if (bc == 0) {
+                    q[a] = (q[a] + N) % N;
+                } else if (q[a] < 0 || q[a] >= N) {
+                    continue;
+                }
+                int64_t j = 0;
+                for (int b = 0; b < g.dims; ++b) j = j * N + q[b];
+                nb += cur[j];
+            }
+        out[lin] = 2.0 * cur[lin] - prev[lin] + lambda2 * c2[lin] * (nb - 2.0 * g.dims * cur[lin]);
+    }
+    if (src) {
+        int64_t j = 0;
+        for (int b = 0; b < g.dims; ++b) j = j * N + src[b];
+        out[j] += amp;
+    }
 }
 
 Mps* box(Mps&& m) { return new Mps(std::move(m)); }
 Mpo* box(Mpo&& m) { return new Mpo(std::move(m)); }
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -806,6 +939,10 @@ Mpo* box(Mpo&& m) { return new Mpo(std::move(m)); }
 // that returns a handle returns a new one.  No call throws or exits.
 // ---------------------------------------------------------------------------
 extern "C" {
+
+// Grids are passed as (dims, n, order): dims 2 or 3, order 0 = SEQUENTIAL,
+// 1 = INTERLEAVED; boundaries as bc 0 = PERIODIC, 1 = ZERO; points as dims
+// ints; dense fields as N^dims doubles in the layout of the Grid comment.
 
 void* oc_mps_from_cores(int d, const int* ranks, const double* data) {
     Mps A;
@@ -832,14 +969,18 @@ void oc_mps_data(const void* h, double* out) {
 }
 void oc_mps_free(void* h) { delete static_cast<Mps*>(h); }
 
-void* oc_mps_from_dense(int n, int order, const double* u, double eps, int chi) {
-    return box(mps_from_dense(u, n, order, eps, chi));
+void* oc_mps_from_dense(int dims, int n, int order, const double* u, double eps, int chi) {
+    return box(mps_from_dense(Grid{dims, n, order}, u, eps, chi));
 }
-void oc_mps_to_dense(const void* h, int n, int order, double* u) { mps_to_dense(*static_cast<const Mps*>(h), n, order, u); }
-void oc_mps_sample(const void* h, int n, int order, int np, const int* ix, const int* iz, double* out) {
-    for (int p = 0; p < np; ++p) out[p] = mps_sample(*static_cast<const Mps*>(h), n, order, ix[p], iz[p]);
+void oc_mps_to_dense(const void* h, int dims, int n, int order, double* u) {
+    mps_to_dense(Grid{dims, n, order}, *static_cast<const Mps*>(h), u);
 }
-void* oc_product_state(int n, int order, int x, int z) { return box(product_state(n, order, x, z)); }
+void oc_mps_sample(const void* h, int dims, int n, int order, int np, const int* pts, double* out) {
+    for (int p = 0; p < np; ++p) out[p] = mps_sample(Grid{dims, n, order}, *static_cast<const Mps*>(h), pts + p * dims);
+}
+void* oc_product_state(int dims, int n, int order, const int* p) {
+    return box(product_state(Grid{dims, n, order}, p));
+}
 void* oc_round(const void* h, double eps, int chi) { return box(tt_round(*static_cast<const Mps*>(h), eps, chi)); }
 void* oc_sum(int nterms, const double* coef, void* const* terms) {
     std::vector<double> c(coef, coef + nterms);
@@ -848,10 +989,17 @@ void* oc_sum(int nterms, const double* coef, void* const* terms) {
     return box(mps_sum(c, t));
 }
 
-void* oc_shift_mpo(int n, int axis, int sign, int bc, int order) { return box(shift_mpo(n, axis, sign, bc, order)); }
-void* oc_laplacian_mpo(int n, int order, int bc) { return box(laplacian_mpo(n, order, bc)); }
-void* oc_laplacian_sum_of_shifts(int n, int order, int bc) { return box(laplacian_sum_of_shifts(n, order, bc)); }
+void* oc_shift_mpo(int dims, int n, int order, int axis, int sign, int bc) {
+    return box(shift_mpo(Grid{dims, n, order}, axis, sign, bc));
+}
+void* oc_laplacian_mpo(int dims, int n, int order, int bc) { return box(laplacian_mpo(Grid{dims, n, order}, bc)); }
+void* oc_laplacian_sum_of_shifts(int dims, int n, int order, int bc) {
+    return box(laplacian_sum_of_shifts(Grid{dims, n, order}, bc));
+}
 void* oc_diagonal_mpo(const void* h) { return box(diagonal_mpo(*static_cast<const Mps*>(h))); }
+void* oc_a_operator_mpo(const void* L, const void* c2, double lambda2) {
+    return box(a_operator_mpo(*static_cast<const Mpo*>(L), *static_cast<const Mps*>(c2), lambda2));
+}
 int oc_mpo_sites(const void* h) { return (int)static_cast<const Mpo*>(h)->size(); }
 void oc_mpo_bonds(const void* h, int* bonds) {
     const Mpo& W = *static_cast<const Mpo*>(h);
@@ -864,8 +1012,8 @@ void oc_mpo_data(const void* h, double* out) {
         out += c.w.size();
     }
 }
-void oc_mpo_grid_operator(const void* h, int n, int order, double* out) {
-    mpo_grid_operator(*static_cast<const Mpo*>(h), n, order, out);
+void oc_mpo_grid_operator(const void* h, int dims, int n, int order, double* out) {
+    mpo_grid_operator(Grid{dims, n, order}, *static_cast<const Mpo*>(h), out);
 }
 void oc_mpo_free(void* h) { delete static_cast<Mpo*>(h); }
 
@@ -876,13 +1024,18 @@ void* oc_zipup_rl(const void* W, const void* A, double eps, int chi) {
     return box(zipup_rl(*static_cast<const Mpo*>(W), *static_cast<const Mps*>(A), eps, chi));
 }
 void* oc_step(const void* L, const void* c2, double lambda2, const void* prev, const void* cur, double eps, int chi,
-              int sx, int sz, double amp, int n, int order) {
-    return box(mps_step(*static_cast<const Mpo*>(L), *static_cast<const Mps*>(c2), lambda2,
-                        *static_cast<const Mps*>(prev), *static_cast<const Mps*>(cur), eps, chi, sx, sz, amp, n, order));
+              const int* src, double amp, int dims, int n, int order) {
+    return box(mps_step(Grid{dims, n, order}, *static_cast<const Mpo*>(L), *static_cast<const Mps*>(c2), lambda2,
+                        *static_cast<const Mps*>(prev), *static_cast<const Mps*>(cur), eps, chi, src, amp));
 }
-void oc_fdtd_step(int N, const double* prev, const double* cur, const double* c2, double lambda2, int bc, int sx,
-                  int sz, double amp, double* out) {
-    fdtd_step(N, prev, cur, c2, lambda2, bc, sx, sz, amp, out);
+void* oc_step_fused(const void* A, const void* prev, const void* cur, double eps, int chi, const int* src, double amp,
+                    int dims, int n, int order) {
+    return box(mps_step_fused(Grid{dims, n, order}, *static_cast<const Mpo*>(A), *static_cast<const Mps*>(prev),
+                              *static_cast<const Mps*>(cur), eps, chi, src, amp));
+}
+void oc_fdtd_step(int dims, int n, const double* prev, const double* cur, const double* c2, double lambda2, int bc,
+                  const int* src, double amp, double* out) {
+    fdtd_step(Grid{dims, n, 0}, prev, cur, c2, lambda2, bc, src, amp, out);
 }
 
 // M (m x n) = U (m x p) diag(S) Vt (p x n), p = min(m, n); returns the sweep

@@ -7,7 +7,7 @@ on its own, against what the paper and the mathematics fix:
 
 * its factorisations: singular values prescribed by construction, orthonormal
   factors, A = Q R with R upper triangular and R^T R = A^T A, the zero and
-  1 x 1 matrices;
+  1 x 1 matrices, columns near the underflow threshold;
 * the Sec. 4.3 truncation rule on hand-made spectra;
 * (b) every shift MPO (Eq. 9-15) contracted to a matrix equals the
   brute-force permutation built from grid indices, and the Laplacian MPO
@@ -18,16 +18,24 @@ on its own, against what the paper and the mathematics fix:
 * (c) a discrete eigenmode follows its closed-form cosine recurrence;
 * (d) separable fields have the closed-form QTT ranks;
 * the leapfrog energy of the untruncated step is conserved;
-* Eckart-Young on constructed spectra through the zip-up and the round.
+* Eckart-Young on constructed spectra through the zip-up and the round;
+* Eq. 7: the transition-operator MPO contracted to a matrix is
+  2I + lambda^2 diag(c^2) times the 5-point stencil, and the untruncated
+  fused step is Eq. 2;
+* 3D (Sec. 6): the 7-point Laplacian MPO is the brute-force stencil, the
+  untruncated 3D step is the dense 7-point update, separable fields have the
+  product of their factors' ranks.
 
-Then the two oracles are compared on truncated steps, where neither is a
-plain definition: ranks equal and dense fields within 1e-10 relative L2."""
+Then the two oracles are compared on truncated steps (2D, fused, 3D), where
+neither is a plain definition: ranks equal and dense fields within 1e-10
+relative L2."""
 import math
 
 import numpy as np
 import pytest
 
 from oracle import cxx as X
+from oracle import qtt3d as Q3
 from oracle import qtt_oracle as O
 import workloads as W
 
@@ -96,6 +104,42 @@ def test_householder_qr_of_dependent_and_zero_columns():
     Q, R = X.qr(A)
     np.testing.assert_allclose(Q.T @ Q, np.eye(4), atol=1e-14)
     np.testing.assert_allclose(Q @ R, A, atol=1e-13)
+
+
+def test_factorisations_of_columns_near_the_underflow_threshold():
+    """Columns of size 1e-160 .. 1e-300 next to columns of size 1: their
+    squares underflow, so a reflector or a rotation built from unscaled
+    sums of squares is not orthogonal.  Both factorisations stay orthogonal
+    and reproduce the matrix to rounding (relative to its norm)."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((6, 9))
+    A[:, 2] *= 1e-160
+    A[:, 5] *= 1e-300
+    A[3, :] *= 1e-170
+    for M in (A, A.T):
+        Q, R = X.qr(M)
+        np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-14)
+        assert np.linalg.norm(Q @ R - M) <= 1e-14 * np.linalg.norm(M)
+        U, S, Vt, sweeps = X.svd(M)
+        assert sweeps >= 0
+        np.testing.assert_allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-13)
+        np.testing.assert_allclose(Vt @ Vt.T, np.eye(Vt.shape[0]), atol=1e-13)
+        assert np.linalg.norm(U @ np.diag(S) @ Vt - M) <= 1e-14 * np.linalg.norm(M)
+        np.testing.assert_allclose(S[:4], np.linalg.svd(M, compute_uv=False)[:4], rtol=1e-13)
+
+
+@pytest.mark.parametrize("sc", [1e-10, 1e-100, 1e-160, 1e-200, 1e-300])
+def test_jacobi_svd_resolves_a_tiny_column_to_relative_accuracy(sc):
+    """[a, sc b]: sigma_1 = |a| and sigma_2 = sc |b - (a.b / a.a) a| up to a
+    relative O(sc^2) (closed form of the 2-column case), which one-sided
+    Jacobi reaches to rounding at any scale the exponent range holds."""
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal(9), rng.standard_normal(9)
+    U, S, Vt, sweeps = X.svd(np.stack([a, sc * b], axis=1))
+    assert sweeps >= 0
+    perp = b - (a @ b) / (a @ a) * a
+    np.testing.assert_allclose(S, [np.linalg.norm(a), sc * np.linalg.norm(perp)], rtol=1e-14)
+    assert abs(U[:, 0] @ U[:, 1]) < 1e-15
 
 
 def test_trunc_rank_rule():
@@ -382,6 +426,175 @@ def test_leapfrog_energy_is_conserved_by_the_untruncated_step(bc):
         prev, cur = cur, X.mps_step(n, order, bc, C, lam2, prev, cur, 0.0, INF)
     E = energy(X.mps_to_dense(prev, n, order), X.mps_to_dense(cur, n, order))
     assert abs(E - E0) < 1e-11 * abs(E0)
+
+
+# ---------------------------------------------------------------------------
+# the transition operator of Eq. 7 and the 3D extension (Sec. 6)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 3])
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_transition_operator_is_the_dense_eq7_operator(n, order, bc):
+    """The MPO of A = 2I + lambda^2 C^2 L contracted to a matrix equals
+    2I + lambda^2 diag(c^2) times the brute-force 5-point stencil."""
+    N = 1 << n
+    rng = np.random.default_rng(n * 10 + len(order) + len(bc))
+    c = rng.uniform(1500.0, 3000.0, (N, N))
+    lam2 = (0.5 / c.max()) ** 2
+    C = X.velocity_mps(c, n, order, 0.0, INF)
+    c2 = X.mps_to_dense(C, n, order)
+    want = 2.0 * np.eye(N * N) + lam2 * c2.reshape(-1)[:, None] * _stencil(n, bc)
+    got = X.a_operator_grid(n, order, bc, C, lam2)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    rc = X.mps_ranks(C)
+    w = [1] + [W_.shape[3] for W_ in X.laplacian_mpo(n, order, bc)]
+    assert X.a_operator_bonds(n, order, bc, C, lam2)[1:-1] == [a * b + 1 for a, b in zip(rc[1:-1], w[1:-1])]
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_untruncated_fused_step_equals_the_dense_update(order, bc):
+    """Eq. 7 in one zip-up with chi = inf, eps = 0 is Eq. 2.  Tolerance: one
+    fused step from a random state is within 1e-14 of Eq. 2 (measured 7e-15;
+    the Jacobi SVD's backward error grows with the rotations each column of
+    the bond r_c w + 1 matrices takes), and the leapfrog carries an error
+    injected at step j into every later step, so after k steps the errors add
+    up to at most k^2 / 2 of one step's: 3.1e-12 at k = 25 (measured
+    1.1e-12 .. 1.3e-12)."""
+    n = 3
+    rng = np.random.default_rng(17)
+    c = rng.uniform(1500.0, 3000.0, (8, 8))
+    lam2 = (0.5 / c.max()) ** 2
+    C = X.velocity_mps(c, n, order, 0.0, INF)
+    c2 = X.mps_to_dense(C, n, order)
+    zero = X.mps_from_dense(np.zeros((8, 8)), n, order, 0.0, INF)
+    prev, cur = zero, zero
+    up, uc = np.zeros((8, 8)), np.zeros((8, 8))
+    for k in range(25):
+        amp = math.cos(0.2 * k) + 0.05 * k
+        prev, cur = cur, X.mps_step_fused(n, order, bc, C, lam2, prev, cur, 0.0, INF, (2, 6), amp)
+        up, uc = uc, X.fdtd_step(up, uc, c2, lam2, bc, (2, 6), amp)
+    assert np.linalg.norm(X.mps_to_dense(cur, n, order) - uc) / np.linalg.norm(uc) < 0.5 * 25 ** 2 * 1e-14
+    # one step from a random state
+    u0, u1 = rng.standard_normal((8, 8)), rng.standard_normal((8, 8))
+    P, Q = X.mps_from_dense(u0, n, order, 0.0, INF), X.mps_from_dense(u1, n, order, 0.0, INF)
+    want = X.fdtd_step(u0, u1, c2, lam2, bc)
+    got = X.mps_to_dense(X.mps_step_fused(n, order, bc, C, lam2, P, Q, 0.0, INF), n, order)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-14
+
+
+def test_truncated_fused_step_agrees_with_the_numpy_oracle():
+    n, chi, eps, order, bc = 5, 16, 1e-7, "interleaved", "periodic"
+    N = 1 << n
+    c = W.layered_model(n, 40.0, 12)
+    lam2 = (0.5 / c.max()) ** 2
+    prev = O.tt_round(W.random_tt_cores(2 * n, chi, 4, decay=0.1), 1e-14, chi)
+    cur = O.tt_round(W.random_tt_cores(2 * n, chi, 5, decay=0.1), 1e-14, chi)
+    A = O.a_operator_mpo(O.laplacian_mpo(n, order, bc), O.velocity_mps(c, n, order, 1e-8, 12), lam2)
+    want = O.mps_step_fused(A, prev, cur, eps, chi, (N // 2 + 1, 3), 0.37, n, order)
+    got = X.mps_step_fused(n, order, bc, X.velocity_mps(c, n, order, 1e-8, 12), lam2, prev, cur, eps, chi,
+                           (N // 2 + 1, 3), 0.37)
+    assert X.mps_ranks(got) == O.mps_ranks(want)
+    ref = O.mps_to_dense(want, n, order)
+    assert np.linalg.norm(X.mps_to_dense(got, n, order) - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def _stencil3(n, bc):
+    N = 1 << n
+    P = N ** 3
+    B = np.zeros((P, P))
+    for x in range(N):
+        for y in range(N):
+            for z in range(N):
+                i = (x * N + y) * N + z
+                B[i, i] = -6.0
+                for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    q = [x + dx, y + dy, z + dz]
+                    if bc == "periodic":
+                        q = [v % N for v in q]
+                    elif not all(0 <= v < N for v in q):
+                        continue
+                    B[i, (q[0] * N + q[1]) * N + q[2]] += 1.0
+    return B
+
+
+@pytest.mark.parametrize("n", [1, 2])
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_3d_laplacian_is_the_seven_point_stencil(n, order, bc):
+    B = _stencil3(n, bc)
+    L = X.laplacian_mpo(n, order, bc, dims=3)
+    assert all(w.shape[0] <= 7 and w.shape[3] <= 7 for w in L)
+    np.testing.assert_array_equal(X.grid_operator("laplacian", n, order, bc, dims=3), B)
+    np.testing.assert_array_equal(X.grid_operator("sum_of_shifts", n, order, bc, dims=3), B)
+    if n == 2:
+        assert [w.shape[3] for w in L] == [w.shape[3] for w in Q3.laplacian_mpo(n, order, bc)]
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("bc", BCS)
+def test_untruncated_3d_step_equals_the_dense_seven_point_update(order, bc):
+    n = 2
+    rng = np.random.default_rng(23)
+    c = rng.uniform(1500.0, 3000.0, (4, 4, 4))
+    lam2 = 0.3 / c.max() ** 2
+    C = X.velocity_mps(c, n, order, 0.0, INF)
+    c2 = X.mps_to_dense(C, n, order, dims=3)
+    np.testing.assert_allclose(c2, c * c, rtol=1e-13)
+    zero = X.mps_from_dense(np.zeros((4, 4, 4)), n, order, 0.0, INF)
+    prev, cur = zero, zero
+    up, uc = np.zeros((4, 4, 4)), np.zeros((4, 4, 4))
+    for k in range(20):
+        amp = math.sin(0.4 * k) + 0.1 * k
+        prev, cur = cur, X.mps_step(n, order, bc, C, lam2, prev, cur, 0.0, INF, (1, 2, 3), amp, dims=3)
+        up, uc = uc, X.fdtd_step(up, uc, c2, lam2, bc, (1, 2, 3), amp)
+    assert np.linalg.norm(X.mps_to_dense(cur, n, order, dims=3) - uc) / np.linalg.norm(uc) < 1e-12
+    # the dense 7-point update is its stencil matrix
+    u0, u1 = rng.standard_normal((4, 4, 4)), rng.standard_normal((4, 4, 4))
+    want = 2 * u1 - u0 + lam2 * c2 * (_stencil3(n, bc) @ u1.reshape(-1)).reshape(4, 4, 4)
+    np.testing.assert_allclose(X.fdtd_step(u0, u1, c2, lam2, bc), want, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_3d_separable_fields_have_the_product_of_their_factor_ranks(order):
+    """f(x) g(y) h(z): the rank at a cut is the product of each factor's QTT
+    rank at the split of its own register (exp: 1, cos: 2 inside the register,
+    a quadratic: min(3, 2^m, 2^(n-m)))."""
+    n = 3
+    N = 1 << n
+    x = np.arange(N, dtype=float)
+    f, rf = np.cos(0.4 * x + 0.3), (lambda m: 1 if m in (0, n) else 2)
+    g, rg = np.exp(0.1 * x), (lambda m: 1)
+    h, rh = 1 + 0.5 * (x / N) - 2 * (x / N) ** 2, (lambda m: min(3, 2 ** m, 2 ** (n - m)))
+    u = f[:, None, None] * g[None, :, None] * h[None, None, :]
+    ranks = X.mps_ranks(X.mps_from_dense(u, n, order, 1e-12, INF))
+    axes = Q3.site_axes(n, order)
+    want = [1]
+    seen = {"x": 0, "y": 0, "z": 0}
+    for a, _b in axes:
+        seen[a] += 1
+        want.append(rf(seen["x"]) * rg(seen["y"]) * rh(seen["z"]))
+    want[-1] = 1
+    assert ranks == want
+
+
+def test_3d_truncated_step_agrees_with_the_numpy_oracle():
+    n, chi, eps, order, bc = 3, 12, 1e-6, "interleaved", "periodic"
+    d = 3 * n
+    rng = np.random.default_rng(31)
+    c = rng.uniform(1500.0, 2500.0, (8, 8, 8))
+    lam2 = 0.3 / c.max() ** 2
+    prev = O.tt_round(W.random_tt_cores(d, chi, 6, decay=0.15), 1e-14, chi)
+    cur = O.tt_round(W.random_tt_cores(d, chi, 7, decay=0.15), 1e-14, chi)
+    want = Q3.mps_step(Q3.laplacian_mpo(n, order, bc), Q3.velocity_mps(c, n, order, 1e-8, 8), lam2, prev, cur,
+                       eps, chi, (3, 4, 5), 0.2, n, order)
+    got = X.mps_step(n, order, bc, X.velocity_mps(c, n, order, 1e-8, 8), lam2, prev, cur, eps, chi, (3, 4, 5), 0.2,
+                     dims=3)
+    assert X.mps_ranks(got) == O.mps_ranks(want)
+    ref = Q3.mps_to_dense(want, n, order)
+    assert np.linalg.norm(X.mps_to_dense(got, n, order, dims=3) - ref) / np.linalg.norm(ref) < 1e-10
+    pts = [(0, 0, 0), (7, 3, 1), (3, 4, 5)]
+    np.testing.assert_allclose(X.mps_sample_points(got, n, order, pts), ref[tuple(np.array(pts).T)], atol=1e-12)
 
 
 # ---------------------------------------------------------------------------
