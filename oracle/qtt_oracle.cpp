@@ -69,16 +69,21 @@ Mat transpose(const Mat& A) {
 // The reflector is built from the column divided by its largest entry (the
 // reflection depends only on the direction): squares of entries near the
 // underflow threshold would otherwise vanish and leave it non-orthogonal.
+// A column with nothing below the diagonal is left as it is (identity, not
+// a sign flip), the convention of the common LAPACK-style QR, so that the
+// two oracles put the bonds in the same gauge: the randomised range finder
+// of the learned form sketches in that gauge.
 void householder_qr(const Mat& A, Mat& Q, Mat& R) {
     const int m = A.m, n = A.n, k = std::min(m, n);
     Mat W = A;
     std::vector<std::vector<double>> refl(k);
     std::vector<double> vnorm2(k, 0.0);
     for (int j = 0; j < k; ++j) {
-        double sc = 0.0;
+        double sc = 0.0, below = 0.0;
         for (int i = j; i < m; ++i) sc = std::max(sc, std::fabs(W(i, j)));
+        for (int i = j + 1; i < m; ++i) below = std::max(below, std::fabs(W(i, j)));
         std::vector<double> v(m - j, 0.0);
-        if (sc == 0.0) {  // nothing to annihilate: identity reflector
+        if (below == 0.0) {  // nothing below the diagonal to annihilate: identity
             refl[j] = std::move(v);
             continue;
         }
@@ -930,6 +935,275 @@ void fdtd_step(const Grid& g, const double* prev, const double* cur, const doubl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Learned rank proposal and randomised rounding (the learned form)
+// ---------------------------------------------------------------------------
+// The paper rounds every bond with a full SVD (Sec. 4.3); the learned form
+// keeps that rule as the arbiter.  A small MLP (40 features -> 128 -> 128 ->
+// 1, ReLU) proposes a bond's rank for the next step from its spectrum; the
+// round then first tries a randomised range finder of width r_hat + p
+// (Halko, Martinsson & Tropp, SIAM Review 2011, Algorithm 4.1 and the direct
+// SVD of Sec. 5.1) and keeps it only if an exact check says the Sec. 4.3 cut
+// is inside the sketch; otherwise the bond takes the full SVD.
+constexpr int kFeat = 40, kWidth = 128, kSpec = 32;
+constexpr int kParams = kWidth * kFeat + kWidth + kWidth * kWidth + kWidth + kWidth + 1;
+
+// The 40 features of a bond's spectrum S (L descending values) after a cut
+// that kept r values, threshold eps, cap chi, bond k of d:
+//   0..31 log10(S_p / S_0) at p = floor(j (L-1) / 31), clipped to [-16, 0],
+//         over 16 (-1 when S_0 or S_p is 0); 32 r / chi; 33 log10 of the
+//         discarded weight over S_0^2, clipped to [-32, 0], over 32 (-1 when
+//         none); 34 log10(eps) / 16; 35 k / d; 36 min(2^k, 2^(d-k), chi) /
+//         chi; 37 #{S_i >= eps S_0} / chi; 38 L / (2 chi); 39 one.
+void rank_features(const double* S, int L, int r, double eps, int chi, int k, int d, double* f) {
+    const double s0 = L > 0 ? S[0] : 0.0;
+    for (int j = 0; j < kSpec; ++j) {
+        const int p = L > 1 ? (j * (L - 1)) / (kSpec - 1) : 0;
+        f[j] = (s0 > 0.0 && L > 0 && S[p] > 0.0) ? std::min(std::max(std::log10(S[p] / s0), -16.0), 0.0) / 16.0 : -1.0;
+    }
+    f[32] = (double)r / chi;
+    double disc = 0.0;
+    for (int i = r; i < L; ++i) disc += S[i] * S[i];
+    f[33] = (s0 > 0.0 && disc > 0.0) ? std::min(std::max(std::log10(disc / (s0 * s0)), -32.0), 0.0) / 32.0 : -1.0;
+    f[34] = eps > 0.0 ? std::log10(eps) / 16.0 : -1.0;
+    f[35] = (double)k / d;
+    f[36] = std::min({std::ldexp(1.0, k), std::ldexp(1.0, d - k), (double)chi}) / chi;
+    int above = 0;
+    if (s0 > 0.0)
+        for (int i = 0; i < L; ++i) above += S[i] >= eps * s0;
+    f[37] = (double)above / chi;
+    f[38] = L / (2.0 * chi);
+    f[39] = 1.0;
+}
+
+// Parameters, flat: W1 (128 x 40), b1, W2 (128 x 128), b2, W3 (1 x 128), b3.
+struct MlpView {
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+    explicit MlpView(const double* p)
+        : W1(p), b1(W1 + kWidth * kFeat), W2(b1 + kWidth), b2(W2 + kWidth * kWidth), W3(b2 + kWidth),
+          b3(W3 + kWidth) {}
+};
+
+// y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for each of the n rows x of X;
+// the pre-activations a1, a2 (n x 128) are kept for the backward pass.
+void mlp_forward(const double* p, const double* X, int n, double* y, std::vector<double>& a1,
+                 std::vector<double>& a2) {
+    const MlpView w(p);
+    a1.assign((size_t)n * kWidth, 0.0);
+    a2.assign((size_t)n * kWidth, 0.0);
+    for (int i = 0; i < n; ++i) {
+        for (int u = 0; u < kWidth; ++u) {
+            double acc = w.b1[u];
+            for (int f = 0; f < kFeat; ++f) acc += w.W1[u * kFeat + f] * X[i * kFeat + f];
+            a1[(size_t)i * kWidth + u] = acc;
+        }
+        for (int u = 0; u < kWidth; ++u) {
+            double acc = w.b2[u];
+            for (int v = 0; v < kWidth; ++v) acc += w.W2[u * kWidth + v] * std::max(a1[(size_t)i * kWidth + v], 0.0);
+            a2[(size_t)i * kWidth + u] = acc;
+        }
+        double acc = w.b3[0];
+        for (int v = 0; v < kWidth; ++v) acc += w.W3[v] * std::max(a2[(size_t)i * kWidth + v], 0.0);
+        y[i] = acc;
+    }
+}
+
+// Mean squared error of y against t and its gradient with respect to every
+// parameter (chain rule through the three layers; ReLU' = [a > 0]).
+double mlp_grad(const double* p, const double* X, const double* t, int n, double* g) {
+    const MlpView w(p);
+    std::vector<double> y(n), a1, a2;
+    mlp_forward(p, X, n, y.data(), a1, a2);
+    std::fill(g, g + kParams, 0.0);
+    double* gW1 = g;
+    double* gb1 = gW1 + kWidth * kFeat;
+    double* gW2 = gb1 + kWidth;
+    double* gb2 = gW2 + kWidth * kWidth;
+    double* gW3 = gb2 + kWidth;
+    double* gb3 = gW3 + kWidth;
+    double loss = 0.0;
+    std::vector<double> da2(kWidth), da1(kWidth);
+    for (int i = 0; i < n; ++i) {
+        const double e = y[i] - t[i];
+        loss += e * e;
+        const double dy = 2.0 * e / n;
+        const double* A1 = &a1[(size_t)i * kWidth];
+        const double* A2 = &a2[(size_t)i * kWidth];
+        gb3[0] += dy;
+        for (int v = 0; v < kWidth; ++v) {
+            gW3[v] += dy * std::max(A2[v], 0.0);
+            da2[v] = A2[v] > 0.0 ? dy * w.W3[v] : 0.0;
+        }
+        for (int u = 0; u < kWidth; ++u) {
+            gb2[u] += da2[u];
+            for (int v = 0; v < kWidth; ++v) gW2[u * kWidth + v] += da2[u] * std::max(A1[v], 0.0);
+        }
+        for (int v = 0; v < kWidth; ++v) {
+            double acc = 0.0;
+            for (int u = 0; u < kWidth; ++u) acc += da2[u] * w.W2[u * kWidth + v];
+            da1[v] = A1[v] > 0.0 ? acc : 0.0;
+        }
+        for (int u = 0; u < kWidth; ++u) {
+            gb1[u] += da1[u];
+            for (int f = 0; f < kFeat; ++f) gW1[u * kFeat + f] += da1[u] * X[i * kFeat + f];
+        }
+    }
+    return loss / n;
+}
+
+// One Adam update (Kingma & Ba, Algorithm 1), step t counted from 1.
+void adam_step(double* p, const double* g, double* m, double* v, int np, int t, double lr, double beta1,
+               double beta2, double eps) {
+    for (int i = 0; i < np; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+        const double mh = m[i] / (1.0 - std::pow(beta1, t)), vh = v[i] / (1.0 - std::pow(beta2, t));
+        p[i] -= lr * mh / (std::sqrt(vh) + eps);
+    }
+}
+
+// The range finder for the Sec. 4.3 cut of X (l x m) from a sketch of its
+// row space with the Gaussian Omega (l x ks):
+//   Y = X^T Omega, Q = qr(Y), B = Q^T X^T, B = Ub diag(Sb) Vb^T,
+//   X ~ Vb diag(Sb) (Q Ub)^T, rho = ||X - X Q Q^T||_F (explicitly).
+// With c = #{Sb_i >= eps Sb_0}: the sketch is rejected when c >= ks (the
+// cut is not inside it); below the cap it is accepted iff rho <= eps Sb_0
+// (every discarded direction of X is then below sqrt(2) eps sigma_1); at
+// the cap iff rho^2 <= ((1 + tau)^2 - 1) sum_{i >= chi} Sb_i^2 (its
+// discarded weight is then within (1 + tau)^2 of the optimum, by Ky Fan's
+// principle on X X^T = A A^T + E E^T).  Outputs: r, Vt (r x m) and
+// US (l x r) with X ~ US Vt, Sb, rho.
+bool range_finder_svd(const Mat& X, const Mat& Om, double eps, int chi, double tau, int& r, Mat& Vt, Mat& US,
+                      std::vector<double>& Sb, double& rho) {
+    const int l = X.m, m = X.n, ks = Om.n;
+    Mat Y(m, ks);  // X^T Omega
+    for (int i = 0; i < l; ++i)
+        for (int a = 0; a < m; ++a) {
+            const double x = X(i, a);
+            for (int j = 0; j < ks; ++j) Y(a, j) += x * Om(i, j);
+        }
+    Mat Q, R;
+    householder_qr(Y, Q, R);
+    const int q = Q.n;
+    Mat XQ(l, q);  // X Q, so B = (X Q)^T
+    for (int i = 0; i < l; ++i)
+        for (int a = 0; a < m; ++a) {
+            const double x = X(i, a);
+            for (int j = 0; j < q; ++j) XQ(i, j) += x * Q(a, j);
+        }
+    const Mat B = transpose(XQ);  // q x l
+    Mat Ub, Vbt;
+    jacobi_svd(B, Ub, Sb, Vbt);
+    double e2 = 0.0;
+    for (int i = 0; i < l; ++i)
+        for (int a = 0; a < m; ++a) {
+            double proj = 0.0;
+            for (int j = 0; j < q; ++j) proj += XQ(i, j) * Q(a, j);
+            const double e = X(i, a) - proj;
+            e2 += e * e;
+        }
+    rho = std::sqrt(e2);
+    const double s0 = Sb.empty() ? 0.0 : Sb[0];
+    int c = 0;
+    if (s0 > 0.0)
+        for (double s : Sb) c += s >= eps * s0;
+    r = trunc_rank(Sb, eps, chi);
+    bool ok;
+    if (s0 == 0.0) {
+        ok = rho == 0.0;
+    } else if (c >= ks) {
+        ok = false;
+    } else if (c < chi) {
+        ok = rho <= eps * s0;
+    } else {
+        double tail = 0.0;
+        for (size_t i = chi; i < Sb.size(); ++i) tail += Sb[i] * Sb[i];
+        ok = rho * rho <= ((1.0 + tau) * (1.0 + tau) - 1.0) * tail;
+    }
+    Vt = Mat(r, m);  // (Q Ub[:, :r])^T
+    for (int j = 0; j < r; ++j)
+        for (int a = 0; a < m; ++a) {
+            double acc = 0.0;
+            for (int b = 0; b < q; ++b) acc += Q(a, b) * Ub(b, j);
+            Vt(j, a) = acc;
+        }
+    US = Mat(l, r);  // Vb[:, :r] diag(Sb[:r])
+    for (int i = 0; i < l; ++i)
+        for (int j = 0; j < r; ++j) US(i, j) = Vbt(j, i) * Sb[j];
+    return ok;
+}
+
+// The round of Sec. 4.3 where bond k of the SVD sweep first tries the range
+// finder of width ks = proposals[k] + p, with Omega the top-left l x ks block
+// of one fixed Gaussian matrix G, when ks < min(l, 2 r_k); rejected or
+// unproposed bonds take the full SVD.  log receives (k, ks, accepted).
+// A G smaller than l x ks makes the bond unproposed.
+Mps tt_round_learned(Mps A, double eps, int chi, const int* proposals, const Mat& G, int p, double tau,
+                     std::vector<int>* log) {
+    const int d = (int)A.size();
+    for (int k = 0; k + 1 < d; ++k) {
+        Mat M(A[k].l * 2, A[k].r);
+        M.a = A[k].a;
+        Mat Q, R;
+        householder_qr(M, Q, R);
+        const int kk = Q.n;
+        Core qc(A[k].l, kk);
+        qc.a = Q.a;
+        const Core& nx = A[k + 1];
+        Core nn(kk, nx.r);
+        for (int i = 0; i < kk; ++i)
+            for (int j = 0; j < nx.l; ++j)
+                for (int s = 0; s < 2; ++s)
+                    for (int e = 0; e < nx.r; ++e) nn.at(i, s, e) += R(i, j) * nx.at(j, s, e);
+        A[k] = std::move(qc);
+        A[k + 1] = std::move(nn);
+    }
+    for (int k = d - 1; k > 0; --k) {
+        const int l = A[k].l, rr2 = 2 * A[k].r;
+        Mat X(l, rr2);
+        X.a = A[k].a;
+        int r = 0;
+        Mat Vt, US;
+        bool done = false;
+        const int ph = proposals ? proposals[k] : 0;
+        // (a G too small for this bond counts as no proposal)
+        if (ph > 0 && ph + p < std::min(l, rr2) && l <= G.m && ph + p <= G.n) {
+            const int ks = ph + p;
+            Mat Om(l, ks);
+            for (int i = 0; i < l; ++i)
+                for (int j = 0; j < ks; ++j) Om(i, j) = G(i, j);
+            std::vector<double> Sb;
+            double rho;
+            const bool ok = range_finder_svd(X, Om, eps, chi, tau, r, Vt, US, Sb, rho);
+            if (log) log->insert(log->end(), {k, ks, ok ? 1 : 0});
+            done = ok;
+        }
+        if (!done) {
+            Mat U, V;
+            std::vector<double> S;
+            jacobi_svd(X, U, S, V);
+            r = trunc_rank(S, eps, chi);
+            Vt = Mat(r, rr2);
+            for (int i = 0; i < r; ++i)
+                for (int j = 0; j < rr2; ++j) Vt(i, j) = V(i, j);
+            US = Mat(l, r);
+            for (int i = 0; i < l; ++i)
+                for (int j = 0; j < r; ++j) US(i, j) = U(i, j) * S[j];
+        }
+        Core v(r, A[k].r);
+        v.a = Vt.a;
+        const Core& pv = A[k - 1];
+        Core np(pv.l, r);
+        for (int a = 0; a < pv.l; ++a)
+            for (int s = 0; s < 2; ++s)
+                for (int j = 0; j < pv.r; ++j)
+                    for (int e = 0; e < r; ++e) np.at(a, s, e) += pv.at(a, s, j) * US(j, e);
+        A[k] = std::move(v);
+        A[k - 1] = std::move(np);
+    }
+    return A;
+}
+
 Mps* box(Mps&& m) { return new Mps(std::move(m)); }
 Mpo* box(Mpo&& m) { return new Mpo(std::move(m)); }
 }  // namespace
@@ -1060,6 +1334,53 @@ void oc_qr(int m, int n, const double* A, double* Q, double* R) {
     householder_qr(a, q, r);
     std::memcpy(Q, q.a.data(), q.a.size() * sizeof(double));
     std::memcpy(R, r.a.data(), r.a.size() * sizeof(double));
+}
+
+// ---- learned form ----
+int oc_mlp_param_count(void) { return kParams; }
+void oc_rank_features(const double* S, int L, int r, double eps, int chi, int k, int d, double* f) {
+    rank_features(S, L, r, eps, chi, k, d, f);
+}
+void oc_mlp_forward(const double* p, const double* X, int n, double* y) {
+    std::vector<double> a1, a2;
+    mlp_forward(p, X, n, y, a1, a2);
+}
+double oc_mlp_grad(const double* p, const double* X, const double* t, int n, double* g) {
+    return mlp_grad(p, X, t, n, g);
+}
+void oc_adam_step(double* p, const double* g, double* m, double* v, int np, int t, double lr, double beta1,
+                  double beta2, double eps) {
+    adam_step(p, g, m, v, np, t, lr, beta1, beta2, eps);
+}
+// Returns accepted (0/1); writes r, Vt (r x m, room for min(l, ks) x m),
+// US (l x r, room for l x min(l, ks)), Sb (room for min(l, ks)) and rho.
+int oc_range_finder_svd(int l, int m, const double* X, int ks, const double* Om, double eps, int chi, double tau,
+                        int* r_out, double* Vt, double* US, double* Sb, int* nsb, double* rho) {
+    Mat x(l, m), om(l, ks);
+    std::memcpy(x.a.data(), X, x.a.size() * sizeof(double));
+    std::memcpy(om.a.data(), Om, om.a.size() * sizeof(double));
+    int r;
+    Mat vt, us;
+    std::vector<double> sb;
+    const bool ok = range_finder_svd(x, om, eps, chi, tau, r, vt, us, sb, *rho);
+    *r_out = r;
+    *nsb = (int)sb.size();
+    std::memcpy(Vt, vt.a.data(), vt.a.size() * sizeof(double));
+    std::memcpy(US, us.a.data(), us.a.size() * sizeof(double));
+    std::memcpy(Sb, sb.data(), sb.size() * sizeof(double));
+    return ok ? 1 : 0;
+}
+// proposals: d ints or null; G (gl x gk) row-major; log: room for 3 (d - 1)
+// ints, *nlog receives the count of ints written.
+void* oc_round_learned(const void* h, double eps, int chi, const int* proposals, int gl, int gk, const double* G,
+                       int p, double tau, int* log, int* nlog) {
+    Mat g(gl, gk);
+    std::memcpy(g.a.data(), G, g.a.size() * sizeof(double));
+    std::vector<int> lg;
+    Mps out = tt_round_learned(*static_cast<const Mps*>(h), eps, chi, proposals, g, p, tau, &lg);
+    std::copy(lg.begin(), lg.end(), log);
+    *nlog = (int)lg.size();
+    return box(std::move(out));
 }
 
 int oc_trunc_rank(int p, const double* s, double eps, int chi) {
