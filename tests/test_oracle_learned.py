@@ -163,6 +163,38 @@ def test_range_finder_acceptance_guarantees_against_brute_force(impl):
     assert all(v > 0 for v in seen.values()), seen
 
 
+def test_acceptance_keeps_its_guarantees_on_narrow_sketches(impl):
+    """Sketches only 1-5 wider than chi, which often miss part of the top
+    chi directions, with eps = 1e-12 (both capped and uncapped cuts occur):
+    every accepted sketch keeps its guarantee (capped: discarded weight
+    within (1+tau)^2 of the optimal tail; uncapped: no discarded direction
+    above sqrt(2) eps sigma_1), and capped acceptances and rejections both
+    occur often."""
+    Ln, _ = impl
+    rng = np.random.default_rng(42)
+    cap = unc = rej = 0
+    for trial in range(200):
+        l, m = int(rng.integers(30, 60)), int(rng.integers(30, 60))
+        n = min(l, m)
+        chi = int(rng.integers(3, n // 2))
+        ks = chi + int(rng.integers(1, 6))
+        X = _with_spectrum(rng, l, m, np.exp(-rng.uniform(0.3, 3.0) * np.arange(n)))
+        eps = 1e-12
+        ok, r, Vt, US, Sb, rho = Ln.range_finder_svd(X, W.gaussian_sketch(500 + trial, l, ks), eps, chi)
+        if not ok:
+            rej += 1
+            continue
+        E = X - X @ (Vt.T @ Vt)
+        sx = np.linalg.svd(X, compute_uv=False)
+        if int(np.count_nonzero(Sb >= eps * Sb[0])) < chi:
+            unc += 1
+            assert np.linalg.norm(E, 2) <= np.sqrt(2.0) * eps * sx[0] * (1 + 1e-9) + 1e-14, trial
+        else:
+            cap += 1
+            assert np.sum(E * E) <= (1 + Ln.TAU) ** 2 * np.sum(sx[chi:] ** 2) * (1 + 1e-9) + 1e-26, trial
+    assert cap > 20 and rej > 20, (cap, unc, rej)
+
+
 def test_learned_round_without_proposals_is_the_plain_round(impl):
     Ln, P = impl
     cores = W.random_tt_cores(10, 16, 4, decay=0.2)
