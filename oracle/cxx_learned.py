@@ -44,7 +44,7 @@ def _lib():
     return lib
 
 
-N_PARAMS = None  # set below from the C++ side
+N_PARAMS = sum(int(np.prod(s)) for s in SHAPES)  # the flat layout; the C++ side reports the same count
 
 
 def _f64(a) -> np.ndarray:
@@ -132,4 +132,7 @@ def tt_round_learned(A: list[np.ndarray], eps: float, chi: int, proposals, G: np
     return out.cores()
 
 
-N_PARAMS = int(_lib().oc_mlp_param_count())
+
+def param_count() -> int:
+    """Parameter count of the C++ oracle's network."""
+    return int(_lib().oc_mlp_param_count())

@@ -229,6 +229,7 @@ def test_learned_round_with_exact_proposals_accepts_and_matches(impl):
 # the two learned-form oracles against each other
 # ---------------------------------------------------------------------------
 def test_learned_forms_agree_on_features_network_and_range_finder():
+    assert cxx_learned.param_count() == cxx_learned.N_PARAMS == learned.N_PARAMS
     rng = np.random.default_rng(21)
     p = W.mlp_params(7).astype(np.float64) + 0.05 * rng.standard_normal(learned.N_PARAMS)
     Xf = rng.standard_normal((9, learned.N_FEAT))
