@@ -13,8 +13,12 @@
 // Acoustic Wave Equation" (Nemeth & Vattay).
 //
 // Besides the 2D step it covers the transition operator of Eq. 7 as one
-// MPO and the fused step, and the 3D extension of Sec. 6 (three registers,
-// the 7-point Laplacian).
+// MPO and the fused step, the 3D extension of Sec. 6 (three registers, the
+// 7-point Laplacian), and the learned form (rank features, the MLP with
+// its gradient and Adam, the randomised range finder with its exact
+// acceptance check, the round that uses it; oracle/cxx_learned.py).  Every
+// function is pinned by tests/test_oracle_cxx.py, tests/test_oracle_learned.py
+// or tests/test_oracle_symmetry.py.
 //
 // Conventions (the readings of the paper are those of the numpy oracle):
 //   * dense fields u[x * N + z], N = 2^n, x horizontal, z depth (Sec. 2,
